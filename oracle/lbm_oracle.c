@@ -1,0 +1,443 @@
+/*
+ * lbm_oracle.c -- plain FP64 CPU oracle of the D2Q9 lattice Boltzmann
+ * cylinder-flow step (Sahiti, Gurugubelli, Surasani, "Lattice Boltzmann
+ * methodology for unconfined flows", arXiv 2605.02185).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or helper with the CUDA
+ * path.  It is written to be read against the paper, not to be fast: every
+ * phase is a whole-lattice loop in the order the paper gives (Section 2.1:
+ * collide, then stream, then the boundary corrections), in IEEE double
+ * precision, compiled without FMA contraction.
+ *
+ * Readings of the paper taken here (the paper is silent or garbled on them):
+ *   - Collision is BGK (Eq. 2) with the equilibrium of Eq. 3; MRT (Eq. 6) is
+ *     not part of this oracle.
+ *   - Streaming is written as a pull: f_i(x) = f*_i(x - c_i).  A source that
+ *     is a solid node gives the half-way bounce-back value f*_opp(i)(x)
+ *     (Section 2.4 and Section 3.1: reflected within the same time step).  A
+ *     source outside the lattice (non-periodic edge) gives the placeholder
+ *     f*_i(x); every such value is overwritten by a boundary rule below
+ *     except where a boundary rule reads it first at a corner.
+ *   - Periodic top/bottom (Eq. 8) is the wrap of the pull source row modulo
+ *     ny (diagonal x shift included).
+ *   - Free-slip (Eq. 7) is the same-node copy of post-stream values:
+ *     top f5=f3, f8=f7, f9=f6; bottom f3=f5, f7=f8, f6=f9 (paper 1-based i).
+ *   - Zou-He top/bottom (Eqs. 9-10) take u = U (the inlet speed) and the
+ *     wall-normal Zou-He density rho_w.
+ *   - The inlet (Section 3.1, "non-equilibrium bounce-back at the inlet") is
+ *     the Zou-He west velocity boundary with velocity (U, 0).
+ *   - The outlet (Eq. 13) copies all nine populations from column nx-2 into
+ *     column nx-1 after the other boundary rules.
+ *   - Boundary order: top row, bottom row (all x), inlet column, outlet
+ *     column (all y).
+ *   - Momentum exchange (Eq. 14): for a resting half-way wall
+ *     f_in = f_out = f*_i(x), so each fluid-to-solid link (c_i pointing into
+ *     the solid) adds 2 f*_i(x) c_i; the sum is the force on the solid.
+ *
+ * A test-only Guo body force and a periodic x mode exist so that the oracle
+ * can be pinned against closed forms (Poiseuille, Taylor-Green); they are not
+ * part of the method.
+ *
+ * Population array layout: f[(k*ny + y)*nx + x], k = i-1 (paper index i).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Table 1 (Section 2.1): velocity set and weights of D2Q9, k = i - 1. */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_WALLS = 3 };
+enum { ORC_X_INOUT = 0, ORC_X_PERIODIC = 1 };
+
+typedef struct {
+  int nx, ny;
+  int bc_y, bc_x;
+  double tau, U;
+  double gx, gy;       /* test-only body force density (Guo forcing) */
+  unsigned char *solid; /* [ny][nx], 1 = solid node */
+  double *f;            /* populations after stream + boundaries, f(n) */
+  double *fs;           /* post-collision populations, f*(n) */
+  double *rowF;         /* [ny][2] per-row force partial sums */
+} orc_t;
+
+#define IDX(o, k, x, y) ((((size_t)(k)) * (size_t)(o)->ny + (size_t)(y)) * (size_t)(o)->nx + (size_t)(x))
+
+/* Opposite direction: the k' with c_k' = -c_k, found by search over Table 1. */
+static int opposite(int k) {
+  for (int j = 0; j < 9; ++j)
+    if (CX[j] == -CX[k] && CY[j] == -CY[k]) return j;
+  return -1;
+}
+
+void orc_constants(int *cx, int *cy, double *w, int *opp) {
+  for (int k = 0; k < 9; ++k) {
+    cx[k] = CX[k];
+    cy[k] = CY[k];
+    w[k] = WT[k];
+    opp[k] = opposite(k);
+  }
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Eq. 3 with c = 1:  f_eq_i = w_i rho [1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 u.u]. */
+void orc_feq(double rho, double ux, double uy, double *feq) {
+  double uu = ux * ux + uy * uy;
+  for (int k = 0; k < 9; ++k) {
+    double cu = CX[k] * ux + CY[k] * uy;
+    feq[k] = WT[k] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+  }
+}
+
+/* Eq. 4: rho = sum_i f_i, rho u = sum_i f_i c_i. */
+void orc_moments(const double *f9, double *rho, double *ux, double *uy) {
+  double r = 0.0, jx = 0.0, jy = 0.0;
+  for (int k = 0; k < 9; ++k) {
+    r += f9[k];
+    jx += f9[k] * CX[k];
+    jy += f9[k] * CY[k];
+  }
+  *rho = r;
+  *ux = jx / r;
+  *uy = jy / r;
+}
+
+/* Eq. 2 right-hand side (BGK): f*_i = f_i - (f_i - f_eq_i(rho, u)) / tau.
+ * With a non-zero body force (test-only) the Guo forcing term is added and u
+ * carries the half-force shift; with gx = gy = 0 this is plain Eq. 2. */
+void orc_collide_node(const double *f9, double tau, double gx, double gy, double *out9) {
+  double rho, ux, uy, feq[9];
+  orc_moments(f9, &rho, &ux, &uy);
+  if (gx == 0.0 && gy == 0.0) {
+    orc_feq(rho, ux, uy, feq);
+    for (int k = 0; k < 9; ++k) out9[k] = f9[k] - (f9[k] - feq[k]) / tau;
+    return;
+  }
+  ux += 0.5 * gx / rho;
+  uy += 0.5 * gy / rho;
+  orc_feq(rho, ux, uy, feq);
+  for (int k = 0; k < 9; ++k) {
+    double cu = CX[k] * ux + CY[k] * uy;
+    double cg = CX[k] * gx + CY[k] * gy;
+    double s = WT[k] * (3.0 * ((CX[k] - ux) * gx + (CY[k] - uy) * gy) + 9.0 * cu * cg);
+    out9[k] = f9[k] - (f9[k] - feq[k]) / tau + (1.0 - 0.5 / tau) * s;
+  }
+}
+
+orc_t *orc_create(int nx, int ny, double tau, double U, int bc_y, int bc_x, const unsigned char *mask) {
+  if (nx < 3 || ny < 3 || !(tau > 0.5)) return NULL;
+  orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
+  if (!o) return NULL;
+  o->nx = nx;
+  o->ny = ny;
+  o->tau = tau;
+  o->U = U;
+  o->bc_y = bc_y;
+  o->bc_x = bc_x;
+  size_t n = (size_t)nx * (size_t)ny;
+  o->solid = (unsigned char *)calloc(n, 1);
+  o->f = (double *)malloc(9 * n * sizeof(double));
+  o->fs = (double *)malloc(9 * n * sizeof(double));
+  o->rowF = (double *)calloc(2 * (size_t)ny, sizeof(double));
+  if (!o->solid || !o->f || !o->fs || !o->rowF) {
+    free(o->solid);
+    free(o->f);
+    free(o->fs);
+    free(o->rowF);
+    free(o);
+    return NULL;
+  }
+  if (mask)
+    for (size_t c = 0; c < n; ++c) o->solid[c] = mask[c] ? 1 : 0;
+  for (int k = 0; k < 9; ++k)
+    for (size_t c = 0; c < n; ++c) {
+      o->f[(size_t)k * n + c] = WT[k];
+      o->fs[(size_t)k * n + c] = WT[k];
+    }
+  return o;
+}
+
+void orc_destroy(orc_t *o) {
+  if (!o) return;
+  free(o->solid);
+  free(o->f);
+  free(o->fs);
+  free(o->rowF);
+  free(o);
+}
+
+void orc_set_body_force(orc_t *o, double gx, double gy) {
+  o->gx = gx;
+  o->gy = gy;
+}
+
+/* f(0) = f_eq(rho0, u0) on fluid nodes; solid nodes hold w_i. */
+void orc_init_equilibrium(orc_t *o, const double *rho, const double *ux, const double *uy) {
+  size_t n = (size_t)o->nx * (size_t)o->ny;
+  for (size_t c = 0; c < n; ++c) {
+    double feq[9];
+    if (o->solid[c])
+      for (int k = 0; k < 9; ++k) feq[k] = WT[k];
+    else
+      orc_feq(rho[c], ux[c], uy[c], feq);
+    for (int k = 0; k < 9; ++k) o->f[(size_t)k * n + c] = feq[k];
+  }
+}
+
+void orc_set_f(orc_t *o, const double *f) { memcpy(o->f, f, 9 * (size_t)o->nx * o->ny * sizeof(double)); }
+void orc_get_f(const orc_t *o, double *f) { memcpy(f, o->f, 9 * (size_t)o->nx * o->ny * sizeof(double)); }
+void orc_set_fs(orc_t *o, const double *fs) { memcpy(o->fs, fs, 9 * (size_t)o->nx * o->ny * sizeof(double)); }
+void orc_get_fs(const orc_t *o, double *fs) { memcpy(fs, o->fs, 9 * (size_t)o->nx * o->ny * sizeof(double)); }
+
+/* Neighbour (x + s*c_k) with the lattice's periodic wraps; 0 if outside. */
+static int neighbour(const orc_t *o, int x, int y, int k, int s, int *nxp, int *nyp) {
+  int xx = x + s * CX[k], yy = y + s * CY[k];
+  if (o->bc_x == ORC_X_PERIODIC) xx = (xx % o->nx + o->nx) % o->nx;
+  if (o->bc_y == ORC_Y_PERIODIC) yy = (yy % o->ny + o->ny) % o->ny;
+  if (xx < 0 || xx >= o->nx || yy < 0 || yy >= o->ny) return 0;
+  *nxp = xx;
+  *nyp = yy;
+  return 1;
+}
+
+/* Collision phase (Eq. 2, Eq. 3, Eq. 4) on every fluid node: f -> f*. */
+void orc_collide(orc_t *o) {
+  int nx = o->nx, ny = o->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      double f9[9], out[9];
+      for (int k = 0; k < 9; ++k) f9[k] = o->f[IDX(o, k, x, y)];
+      if (o->solid[c])
+        for (int k = 0; k < 9; ++k) out[k] = f9[k];
+      else
+        orc_collide_node(f9, o->tau, o->gx, o->gy, out);
+      for (int k = 0; k < 9; ++k) o->fs[IDX(o, k, x, y)] = out[k];
+    }
+}
+
+/* Momentum exchange, Eq. 14: F = sum over fluid nodes x and directions i
+ * with x + c_i solid of 2 f*_i(x) c_i.  Row partials are summed in row order,
+ * so the result does not depend on the thread count. */
+void orc_force(orc_t *o, double *F) {
+  int nx = o->nx, ny = o->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y) {
+    double fx = 0.0, fy = 0.0;
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[(size_t)y * nx + x]) continue;
+      for (int k = 1; k < 9; ++k) {
+        int tx, ty;
+        if (!neighbour(o, x, y, k, +1, &tx, &ty)) continue;
+        if (!o->solid[(size_t)ty * nx + tx]) continue;
+        double v = 2.0 * o->fs[IDX(o, k, x, y)];
+        fx += v * CX[k];
+        fy += v * CY[k];
+      }
+    }
+    o->rowF[2 * y] = fx;
+    o->rowF[2 * y + 1] = fy;
+  }
+  double fx = 0.0, fy = 0.0;
+  for (int y = 0; y < ny; ++y) {
+    fx += o->rowF[2 * y];
+    fy += o->rowF[2 * y + 1];
+  }
+  F[0] = fx;
+  F[1] = fy;
+}
+
+/* Streaming phase (left side of Eq. 2), pull form, with half-way bounce-back
+ * on solid sources and the placeholder for sources outside the lattice. */
+void orc_stream(orc_t *o) {
+  int nx = o->nx, ny = o->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[(size_t)y * nx + x]) continue;
+      for (int k = 0; k < 9; ++k) {
+        int sx, sy;
+        double v;
+        if (!neighbour(o, x, y, k, -1, &sx, &sy))
+          v = o->fs[IDX(o, k, x, y)];
+        else if (o->solid[(size_t)sy * nx + sx])
+          v = o->fs[IDX(o, opposite(k), x, y)];
+        else
+          v = o->fs[IDX(o, k, sx, sy)];
+        o->f[IDX(o, k, x, y)] = v;
+      }
+    }
+}
+
+/* Section 2.3.1, Eq. 7a (top) and Eq. 7b (bottom).  Paper indices 1-based;
+ * here f[k] with k = i - 1. */
+static void freeslip_top(double *f) {
+  f[4] = f[2]; /* f5 = f3 */
+  f[7] = f[6]; /* f8 = f7 */
+  f[8] = f[5]; /* f9 = f6 */
+}
+static void freeslip_bottom(double *f) {
+  f[2] = f[4]; /* f3 = f5 */
+  f[6] = f[7]; /* f7 = f8 */
+  f[5] = f[8]; /* f6 = f9 */
+}
+
+/* Section 2.3.3, Eq. 9a-c (top), wall velocity (u, 0) = (U, 0); rho is the
+ * Zou-He wall density rho_w = f1 + f2 + f4 + 2 (f3 + f6 + f7). */
+static void zouhe_top(double *f, double U) {
+  double rho = f[0] + f[1] + f[3] + 2.0 * (f[2] + f[5] + f[6]);
+  f[4] = f[2];                                         /* f5 = f3 */
+  f[7] = f[5] + 0.5 * (f[1] - f[3]) - 0.5 * rho * U;  /* f8 */
+  f[8] = f[6] - 0.5 * (f[1] - f[3]) + 0.5 * rho * U;  /* f9 */
+}
+/* Eq. 10a-c (bottom); rho_w = f1 + f2 + f4 + 2 (f5 + f8 + f9). */
+static void zouhe_bottom(double *f, double U) {
+  double rho = f[0] + f[1] + f[3] + 2.0 * (f[4] + f[7] + f[8]);
+  f[2] = f[4];                                         /* f3 = f5 */
+  f[5] = f[7] - 0.5 * (f[1] - f[3]) + 0.5 * rho * U;  /* f6 */
+  f[6] = f[8] + 0.5 * (f[1] - f[3]) - 0.5 * rho * U;  /* f7 */
+}
+
+/* Inlet, Section 3.1: Zou-He (non-equilibrium bounce-back) velocity
+ * boundary on the west side with velocity (U, 0); unknowns f2, f6, f9. */
+static void zouhe_inlet(double *f, double U) {
+  double rho = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - U);
+  f[1] = f[3] + (2.0 / 3.0) * rho * U;                       /* f2 */
+  f[5] = f[7] - 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * U; /* f6 */
+  f[8] = f[6] + 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * U; /* f9 */
+}
+
+static void load9(const orc_t *o, int x, int y, double *f) {
+  for (int k = 0; k < 9; ++k) f[k] = o->f[IDX(o, k, x, y)];
+}
+static void store9(orc_t *o, int x, int y, const double *f) {
+  for (int k = 0; k < 9; ++k) o->f[IDX(o, k, x, y)] = f[k];
+}
+
+/* Boundary phase (Section 2.3, applied after streaming): top row, bottom
+ * row, inlet column, outlet column (Eq. 13). */
+void orc_boundaries(orc_t *o) {
+  int nx = o->nx, ny = o->ny;
+  double f[9];
+  if (o->bc_y == ORC_Y_FREESLIP || o->bc_y == ORC_Y_ZOUHE) {
+    for (int x = 0; x < nx; ++x) {
+      int y = ny - 1;
+      if (o->solid[(size_t)y * nx + x]) continue;
+      load9(o, x, y, f);
+      if (o->bc_y == ORC_Y_FREESLIP)
+        freeslip_top(f);
+      else
+        zouhe_top(f, o->U);
+      store9(o, x, y, f);
+    }
+    for (int x = 0; x < nx; ++x) {
+      int y = 0;
+      if (o->solid[(size_t)y * nx + x]) continue;
+      load9(o, x, y, f);
+      if (o->bc_y == ORC_Y_FREESLIP)
+        freeslip_bottom(f);
+      else
+        zouhe_bottom(f, o->U);
+      store9(o, x, y, f);
+    }
+  }
+  if (o->bc_x == ORC_X_INOUT) {
+    for (int y = 0; y < ny; ++y) {
+      if (o->solid[(size_t)y * nx]) continue;
+      load9(o, 0, y, f);
+      zouhe_inlet(f, o->U);
+      store9(o, 0, y, f);
+    }
+    for (int y = 0; y < ny; ++y) {
+      load9(o, nx - 2, y, f);
+      store9(o, nx - 1, y, f);
+    }
+  }
+}
+
+/* One time step n -> n+1 in the paper's order (Section 2.1): collide, the
+ * force of Eq. 14 from f*(n), stream, boundary corrections.  Fhist receives
+ * (Fx, Fy) of each step if not NULL. */
+void orc_run(orc_t *o, long nsteps, double *Fhist) {
+  for (long s = 0; s < nsteps; ++s) {
+    double F[2];
+    orc_collide(o);
+    orc_force(o, F);
+    if (Fhist) {
+      Fhist[2 * s] = F[0];
+      Fhist[2 * s + 1] = F[1];
+    }
+    orc_stream(o);
+    orc_boundaries(o);
+  }
+}
+
+/* Moments of the current f (Eq. 4); solid nodes report rho = 1, u = 0.  With
+ * the test-only body force the velocity carries the half-force shift. */
+void orc_fields(const orc_t *o, double *rho, double *ux, double *uy) {
+  int nx = o->nx, ny = o->ny;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      size_t c = (size_t)y * nx + x;
+      if (o->solid[c]) {
+        rho[c] = 1.0;
+        ux[c] = 0.0;
+        uy[c] = 0.0;
+        continue;
+      }
+      double f9[9], r, u, v;
+      load9(o, x, y, f9);
+      orc_moments(f9, &r, &u, &v);
+      rho[c] = r;
+      ux[c] = u + 0.5 * o->gx / r;
+      uy[c] = v + 0.5 * o->gy / r;
+    }
+}
+
+/* Brute-force list of fluid-to-solid links (x, y, k) with x + c_k solid, in
+ * row-major then direction order.  Returns the number of links (all of them
+ * are counted; at most cap are written). */
+long orc_links(const orc_t *o, int *out, long cap) {
+  long n = 0;
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      if (o->solid[(size_t)y * o->nx + x]) continue;
+      for (int k = 1; k < 9; ++k) {
+        int tx, ty;
+        if (!neighbour(o, x, y, k, +1, &tx, &ty)) continue;
+        if (!o->solid[(size_t)ty * o->nx + tx]) continue;
+        if (n < cap) {
+          out[3 * n] = x;
+          out[3 * n + 1] = y;
+          out[3 * n + 2] = k;
+        }
+        ++n;
+      }
+    }
+  return n;
+}
