@@ -1,0 +1,183 @@
+/*
+ * gblbm.h -- C ABI of the GB300 (sm_103a) D2Q9 lattice Boltzmann solver for
+ * unconfined flow past a cylinder (Sahiti, Gurugubelli, Surasani, "Lattice
+ * Boltzmann methodology for unconfined flows", arXiv 2605.02185).
+ *
+ * One time step, as the paper defines it (Section 2.1), is: BGK collision
+ * (Eq. 2) towards the equilibrium of Eq. 3 with the moments of Eq. 4;
+ * streaming; then the boundary corrections of Section 2.3 -- top/bottom
+ * free-slip (Eq. 7), periodic (Eq. 8) or Zou-He velocity (Eqs. 9-10), the
+ * Zou-He uniform inlet (Section 3.1) and the zero-gradient outlet (Eq. 13) --
+ * with half-way bounce-back on the staircased cylinder (Section 2.4,
+ * Section 3.1).  Every step also forms the momentum-exchange force on the
+ * cylinder (Eq. 14) and thereby the drag and lift coefficients (Eq. 15).
+ *
+ * The library keeps the post-collision populations f* resident on the GPU and
+ * runs each step as ONE fused kernel: pull-stream from the previous f*, the
+ * boundary rules, the collision, the store of the new f*, and the force
+ * partial sums of the cylinder links, reduced in a fixed order into a double
+ * precision history on the device.
+ *
+ * Conventions for every function below:
+ *   - Return value 0 (LBM_OK) or a negative LBM_ERR_* code; nothing throws.
+ *   - Host pointers are read or written synchronously before return; the
+ *     caller keeps ownership.  Device pointers are named as such.
+ *   - Lattice arrays on the host are row-major [ny][nx] (index y*nx + x),
+ *     y = 0 the bottom row, x = 0 the inlet column.
+ *   - Populations use the paper's direction order i = 1..9 (Table 1) as
+ *     plane index k = i - 1.
+ *   - All work of one context runs in order on one CUDA stream.
+ */
+#ifndef GBLBM_H
+#define GBLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)      /* invalid argument or geometry */
+#define LBM_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define LBM_ERR_UNSTABLE (-3) /* |u| > 0.3 or NaN seen on a fluid node */
+#define LBM_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define LBM_ERR_OOM (-5)      /* device memory or workspace too small */
+#define LBM_ERR_RANGE (-6)    /* requested history entries not available */
+#define LBM_ERR_STATE (-7)    /* call out of order (e.g. step before init) */
+
+/* ---- top/bottom boundary modes (Section 2.3) --------------------------- */
+#define LBM_BC_FREESLIP 0 /* Eq. 7: specular same-node copy */
+#define LBM_BC_PERIODIC 1 /* Eq. 8: wrap in y */
+#define LBM_BC_ZOUHE 2    /* Eqs. 9-10: Zou-He velocity (U, 0) */
+
+/* ---- population storage ------------------------------------------------ */
+#define LBM_F32 0      /* float, stored as offsets f_i - w_i */
+#define LBM_F16_OFS 1  /* IEEE half offsets f_i - w_i, float arithmetic */
+#define LBM_BF16_OFS 2 /* bfloat16 offsets f_i - w_i, float arithmetic */
+#define LBM_F64 3      /* double offsets, double arithmetic */
+
+/* ---- step kernel variants --------------------------------------------- */
+#define LBM_KERNEL_AUTO 0   /* the TMA-staged kernel with the tuned shape */
+#define LBM_KERNEL_DIRECT 1 /* one thread per cell, loads straight from HBM */
+#define LBM_KERNEL_TMA 2    /* persistent; bulk-async (TMA) row staging */
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Creation options.  Fill with lbm_opts_default() and override fields. */
+typedef struct lbm_opts {
+  int nx, ny;          /* lattice size, nodes; both >= 5 */
+  double tau;          /* BGK relaxation time (Eq. 2), > 0.5 */
+  double U;            /* inlet speed, lattice units, 0 <= U < 0.3 */
+  int bc_top_bottom;   /* LBM_BC_* */
+  int storage;         /* LBM_F32 etc. */
+  double D_ref;        /* length in Eq. 15; <= 0: (rows holding solid) - 1 */
+  double rho_in;       /* density in Eq. 15; <= 0: 1 */
+  int64_t history_capacity; /* force-history ring entries; <= 0: 1 << 20 */
+  int kernel;          /* LBM_KERNEL_* */
+  int consumer_warps;  /* TMA kernel: compute warps per CTA (0: tuned) */
+  int cells_per_thread;/* TMA kernel: cells per compute thread per row tile */
+  int stages;          /* TMA kernel: pipeline depth (row tiles in flight) */
+  int ctas_per_sm;     /* TMA kernel: resident CTAs per SM (0: 1) */
+  int graph_steps;     /* steps per captured CUDA graph (even); 0: auto; < 0: none */
+  void *stream;        /* cudaStream_t to run on; NULL: the context makes its own */
+  void *workspace;     /* device memory >= lbm_workspace_bytes(); NULL: the library allocates */
+  size_t workspace_bytes;
+} lbm_opts;
+
+/* Defaults: F32 storage, auto kernel, free-slip, capacity 1 << 20. */
+int lbm_opts_default(lbm_opts *opts);
+
+/* Bytes of device workspace lbm_create_ex needs for opts and this mask
+ * (host, [ny][nx], 1 = solid).  Lets a caller hand in memory it allocated
+ * (e.g. a torch tensor) instead of letting the library allocate. */
+int lbm_workspace_bytes(const lbm_opts *opts, const uint8_t *mask, size_t *bytes);
+
+/* Create a lattice.  mask: host [ny][nx], nonzero = solid node of the
+ * staircased body (Section 2.4).  Solid nodes must lie in
+ * 2 <= x <= nx-3, 2 <= y <= ny-3 (the inlet, outlet and wall rules assume
+ * fluid there).  The populations start at rest (rho = 1, u = 0); call
+ * lbm_init_fields before stepping. */
+int lbm_create(int nx, int ny, double tau, double U, const uint8_t *mask, int bc_top_bottom,
+               lbm_ctx **out);
+int lbm_create_ex(const lbm_opts *opts, const uint8_t *mask, lbm_ctx **out);
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Initial state: f(0) = f_eq(rho, u) of Eq. 3 on fluid nodes (host double
+ * arrays [ny][nx]), then the first collision, so the device holds f*(0), and
+ * history entry 0 = the Eq. 14 force of f*(0).  Resets the history. */
+int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, const double *v);
+
+/* Advance n >= 0 steps (asynchronous on the context stream).  Step n maps
+ * f*(n-1) to f*(n) and appends the force of f*(n) to the history. */
+int lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Wait for the context stream; report LBM_ERR_UNSTABLE / LBM_ERR_TIMEOUT if
+ * a step flagged one since the last lbm_init_fields. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Number of force-history entries (= steps + 1 after init). */
+int lbm_force_count(lbm_ctx *ctx, int64_t *count);
+
+/* Drag and lift coefficients (Eq. 15, Cd = Fx / (rho_in U^2 D / 2)) of
+ * history entries [first, first + n) into host arrays.  LBM_ERR_RANGE if an
+ * entry is not yet written or already overwritten in the ring. */
+int lbm_forces(lbm_ctx *ctx, int64_t first, int64_t n, double *cd, double *cl);
+
+/* The same entries as raw lattice-unit forces (Eq. 14), host [n][2]. */
+int lbm_forces_raw(lbm_ctx *ctx, int64_t first, int64_t n, double *fxy);
+
+/* Reference length and density used by lbm_forces. */
+int lbm_set_reference(lbm_ctx *ctx, double D_ref, double rho_in);
+
+/* Moments (Eq. 4) of the current f*, which equal those of the post-boundary
+ * f of the same step; solid nodes report rho = 1, u = v = 0.
+ * dtype 0: float arrays, 1: double arrays; host [ny][nx] each. */
+int lbm_fields(lbm_ctx *ctx, int dtype, void *rho, void *u, void *v);
+
+/* The same into DEVICE float arrays [ny][nx] (asynchronous). */
+int lbm_fields_device(lbm_ctx *ctx, float *rho, float *u, float *v);
+
+/* Double-precision sum of rho over fluid nodes (mass-drift check). */
+int lbm_mass(lbm_ctx *ctx, double *mass);
+
+/* Checkpoint: the current f* as stored offsets f*_i - w_i, packed host
+ * [9][ny][nx] of the storage type (4, 2, 2 or 8 bytes per value).
+ * bytes must equal 9 * nx * ny * element size. */
+int lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
+/* Restore a checkpoint written by lbm_get_populations.  history_count is
+ * the lbm_force_count value at the time of the checkpoint; the next step
+ * writes history entry history_count.  Earlier history entries are not
+ * restored. */
+int lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes, int64_t history_count);
+
+/* A rectangular window [x0, x0+w) x [y0, y0+h) of the current f* offsets,
+ * packed host [9][h][w] of the storage type (probes, sampled checks). */
+int lbm_get_window(lbm_ctx *ctx, int x0, int y0, int w, int h, void *dst);
+
+/* Switch the step kernel (LBM_KERNEL_*) and its shape; re-captures graphs. */
+int lbm_set_kernel(lbm_ctx *ctx, int kernel, int consumer_warps, int cells_per_thread, int stages,
+                   int ctas_per_sm);
+/* The kernel shape in use: kernel, consumer warps, cells/thread, stages,
+ * CTAs per SM, grid size (CTAs) -- 6 ints. */
+int lbm_get_kernel(lbm_ctx *ctx, int *out6);
+
+/* The CUDA stream the context launches on (cudaStream_t). */
+int lbm_get_stream(lbm_ctx *ctx, void **stream);
+
+/* Step-kernel launches issued since creation (counts each kernel once). */
+int lbm_launch_count(lbm_ctx *ctx, int64_t *count);
+
+/* Algorithmic bytes one step moves through HBM: 2 * 9 * element size per
+ * node (read f*(n-1), write f*(n)). */
+int lbm_bytes_per_step(lbm_ctx *ctx, double *bytes);
+
+const char *lbm_error_string(int code);
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLBM_H */

@@ -1,0 +1,54 @@
+// lbm_internal.h -- interfaces between the C ABI layer and the per-storage
+// kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace gblbm {
+
+struct StepParams;
+
+// Launchers of one storage type.  All launches are asynchronous on `st`.
+struct KernelOps {
+  int elem;  // bytes per stored population value
+  cudaError_t (*direct)(const void *A, void *B, const StepParams &p, cudaStream_t st);
+  cudaError_t (*tma)(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st);
+  cudaError_t (*prep)(int shape);  // set the dynamic shared memory limit of a TMA shape
+  int (*occupancy)(int shape);     // resident CTAs per SM of a TMA shape (0: does not fit)
+  size_t (*smem)(int shape);
+  cudaError_t (*init)(void *A, const StepParams &p, const double *rho, const double *u, const double *v, int y0,
+                      int rows, cudaStream_t st);
+  cudaError_t (*force)(const void *A, const StepParams &p, cudaStream_t st);
+  cudaError_t (*fields)(const void *A, const StepParams &p, void *rho, void *u, void *v, int dbl, int y0, int rows,
+                        cudaStream_t st);
+  cudaError_t (*mass_rows)(const void *A, const StepParams &p, double *part, int y0, int rows, cudaStream_t st);
+};
+
+const KernelOps *ops_f32();
+const KernelOps *ops_f16();
+const KernelOps *ops_bf16();
+const KernelOps *ops_f64();
+
+// TMA kernel shapes X(id, compute warps, cells per thread, stages).
+#define GBLBM_TMA_SHAPES(X) \
+  X(0, 8, 4, 4)             \
+  X(1, 8, 2, 6)             \
+  X(2, 16, 2, 3)            \
+  X(3, 16, 1, 6)            \
+  X(4, 8, 1, 8)             \
+  X(5, 4, 4, 8)             \
+  X(6, 8, 2, 4)             \
+  X(7, 4, 2, 6)             \
+  X(8, 8, 1, 4)             \
+  X(9, 4, 2, 4)
+
+struct TmaShape {
+  int ncw, cpt, stages;
+};
+#define GBLBM_SHAPE_ENTRY(id, a, b, c) {a, b, c},
+constexpr TmaShape kTmaShapes[] = {GBLBM_TMA_SHAPES(GBLBM_SHAPE_ENTRY)};
+#undef GBLBM_SHAPE_ENTRY
+constexpr int kNumTmaShapes = (int)(sizeof(kTmaShapes) / sizeof(kTmaShapes[0]));
+
+}  // namespace gblbm

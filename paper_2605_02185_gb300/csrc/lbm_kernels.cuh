@@ -1,0 +1,438 @@
+// lbm_kernels.cuh -- the fused D2Q9 step kernels and their helpers, as
+// templates over the population storage type.  Each lbm_k_<type>.cu
+// instantiates them for one type and exports a KernelOps table.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace gblbm {
+
+// Post one row tile's force partial to its slot; the tile that posts last in
+// the step reduces all slots (fixed order) into the history.  Called
+// uniformly by all nthr threads of the group; sync() is the group barrier.
+template <int NW, class Sync>
+__device__ __forceinline__ void post_force(const StepParams &p, int y, int s, double fx, double fy, int tid,
+                                           double (&red)[2][NW], int &s_last, Sync sync) {
+  const int warp = tid >> 5, lane = tid & 31;
+  fx = warp_sum(fx);
+  fy = warp_sum(fy);
+  if (lane == 0) {
+    red[0][warp] = fx;
+    red[1][warp] = fy;
+  }
+  sync();
+  if (tid == 0) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      sx += red[0][w];
+      sy += red[1][w];
+    }
+    const int slot = (y - p.fy0) * (p.fs1 - p.fs0 + 1) + (s - p.fs0);
+    __stcg(p.slots + slot, make_double2(sx, sy));
+    __threadfence();
+    const unsigned prev = atomicAdd(p.done, 1u);
+    s_last = (prev == (unsigned)(p.nslots - 1)) ? 1 : 0;
+    if (s_last) __threadfence();
+  }
+  sync();
+  if (s_last && warp == 0) finish_force(p, lane);
+}
+
+__device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s) {
+  return y >= p.fy0 && y <= p.fy1 && s >= p.fs0 && s <= p.fs1;
+}
+
+// One node: pull, boundary rules, collision; stores g*(x) into B.
+template <class S, class Fetch>
+__device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
+                                            int y, typename Store<S>::C omega, Fetch fetch, double &fx, double &fy,
+                                            bool &bad) {
+  using C = typename Store<S>::C;
+  const int xe = (x == p.nx - 1) ? p.nx - 2 : x;  // Eq. 13: outlet = column nx-2
+  const uint32_t lm = link_mask(p, xe, y);
+  C g[9];
+  if (lm & LM_SOLID) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = (C)0;
+  } else {
+    pull<S>(A, p, xe, y, lm, fetch, g);
+    boundaries<C>(g, xe, y, p);
+    const C uu = collide<C>(g, omega);
+    bad |= !(uu <= (C)0.09);
+    if ((lm & LM_LINKS) && x == xe) link_force<C>(g, lm, fx, fy);
+  }
+  const size_t o = (size_t)y * p.pitch + x;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[(size_t)k * p.plane + o] = Store<S>::st(g[k]);
+}
+
+// ---- direct kernel: one CTA per row tile, loads straight from HBM -------
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
+  using C = typename Store<S>::C;
+  __shared__ double red[2][NT / 32];
+  __shared__ int s_last;
+  const int t = blockIdx.x;
+  const int y = t / p.nseg, s = t - y * p.nseg;
+  const int x0 = s * p.seg;
+  const int x1 = min(x0 + p.seg, p.nx);
+  const C omega = (C)p.omega;
+  double fx = 0.0, fy = 0.0;
+  bool bad = false;
+  auto fetch = [&](int k, int sx, int sy) -> C {
+    return Store<S>::ld(__ldg(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
+  };
+  for (int x = x0 + (int)threadIdx.x; x < x1; x += NT) update_node<S>(A, B, p, x, y, omega, fetch, fx, fy, bad);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
+  if (is_force_item(p, y, s))
+    post_force<NT / 32>(p, y, s, fx, fy, (int)threadIdx.x, red, s_last, [] { __syncthreads(); });
+}
+
+// ---- TMA-staged persistent kernel ----------------------------------------
+// CTA = NCW compute warps + 1 producer warp.  The producer's elected lane
+// walks the CTA's row tiles (grid-stride) and, per tile, issues nine 1-D bulk
+// async copies -- for plane k the row y - c_ky, columns [x0 - H, x0 + W + H)
+// -- into a STAGES-deep ring of shared-memory tiles, signalling an mbarrier
+// with the byte count.  Compute warps wait on it, pull from shared memory
+// (any x shift, no bank conflicts: consecutive lanes read consecutive
+// elements), apply the boundary rules, collide and store straight to HBM
+// with coalesced stores, then release the stage.  Every wait is bounded.
+template <class S, int NCW, int CPT, int STAGES>
+__global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
+  using C = typename Store<S>::C;
+  constexpr int H = 16 / (int)sizeof(S);
+  constexpr int NC = NCW * 32;
+  constexpr int W = NC * CPT;
+  constexpr int SEG = W + 2 * H;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S *tiles = reinterpret_cast<S *>(smem);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
+  __shared__ double red[2][NCW];
+  __shared__ int s_last;
+  __shared__ int s_abort_store;
+  volatile int *s_abort = &s_abort_store;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = p.ny * p.nseg;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(smem_addr(&bars[q]), 1);
+      mbar_init(smem_addr(&bars[STAGES + q]), NCW);
+    }
+    *s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NCW) {  // ---------------- producer
+    if (lane == 0) {
+      int j = 0;
+      for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+        const int st = j % STAGES;
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+          if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
+          *s_abort = 1;
+          break;
+        }
+        if (*s_abort) break;
+        const int y = t / p.nseg, s = t - y * p.nseg;
+        const int x0 = s * W;
+        const int xs = max(x0 - H, 0), xl = min(x0 + W + H, p.pitch);
+        const uint32_t bytes = (uint32_t)(xl - xs) * (uint32_t)sizeof(S);
+        int rows[9];
+        uint32_t total = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          int sy = y - CY(k);
+          if (p.bc == BC_PERIODIC) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+          rows[k] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
+          total += rows[k] >= 0 ? bytes : 0u;
+        }
+        const uint32_t fb = smem_addr(&bars[st]);
+        mbar_arrive_expect_tx(fb, total);
+        S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (rows[k] >= 0)
+            bulk_g2s(smem_addr(dst + (size_t)k * SEG), A + (size_t)k * p.plane + (size_t)rows[k] * p.pitch + xs, bytes,
+                     fb);
+      }
+      // Do not leave while a copy into this CTA's shared memory is in flight.
+      for (int q = max(0, j - STAGES); q < j; ++q) {
+        const uint32_t fb = smem_addr(&bars[q % STAGES]);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
+          if (global_ns() - t0 > 1000000000ull) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------------- compute warps
+  const int ctid = threadIdx.x;
+  const C omega = (C)p.omega;
+  bool bad = false;
+  int j = 0;
+  for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+    const int st = j % STAGES;
+    bool ok = false;
+    if (!*s_abort) {
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      if (!ok && !*s_abort) {
+        atomicOr(p.err, ERR_TIMEOUT);
+        *s_abort = 1;
+      }
+    }
+    const int y = t / p.nseg, s = t - y * p.nseg;
+    const int x0 = s * W;
+    double fx = 0.0, fy = 0.0;
+    if (ok) {
+      const S *tile = tiles + (size_t)st * 9 * SEG + (H - x0);
+      auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int x = x0 + c * NC + ctid;
+        if (x < p.nx) update_node<S>(A, B, p, x, y, omega, fetch, fx, fy, bad);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
+    }
+    if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+}
+
+template <class S, int NCW, int CPT, int STAGES>
+constexpr size_t tma_smem_bytes() {
+  return (size_t)STAGES * 9 * (NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t);
+}
+
+// ---- initial state: f*(0) = f_eq(rho0, u0), Eq. 3, as offsets ----------
+template <class S>
+__global__ void init_kernel(S *__restrict__ A, StepParams p, const double *__restrict__ rho,
+                            const double *__restrict__ u, const double *__restrict__ v, int y0, int rows) {
+  const long long n = (long long)rows * p.nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = y0 + (int)(i / p.nx);
+    const uint32_t lm = link_mask(p, x, y);
+    const size_t o = (size_t)y * p.pitch + x;
+    if (lm & LM_SOLID) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) A[(size_t)k * p.plane + o] = Store<S>::st(0);
+      continue;
+    }
+    const double r = rho[i], ux = u[i], uy = v[i];
+    const double base = (r - 1.0) - 1.5 * r * (ux * ux + uy * uy);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double cu = CX(k) * ux + CY(k) * uy;
+      const double geq = WD(k) * (base + r * cu * (3.0 + 4.5 * cu));
+      A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)geq);
+    }
+  }
+}
+
+// ---- Eq. 14 force of the stored f*, one CTA, fixed order -----------------
+template <class S>
+__global__ void __launch_bounds__(256) force_kernel(const S *__restrict__ A, StepParams p) {
+  __shared__ double rx[256], ry[256];
+  double fx = 0.0, fy = 0.0;
+  const int n = p.lw * p.lh;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const uint32_t lm = p.lmap[i];
+    if ((lm & LM_SOLID) || !(lm & LM_LINKS)) continue;
+    const int x = p.lx0 + i % p.lw, y = p.ly0 + i / p.lw;
+    const size_t o = (size_t)y * p.pitch + x;
+#pragma unroll
+    for (int d = 1; d < 9; ++d)
+      if (lm & (1u << OPP(d))) {
+        const double g = (double)Store<S>::ld(A[(size_t)d * p.plane + o]);
+        fx += 2.0 * g * CX(d);
+        fy += 2.0 * g * CY(d);
+      }
+  }
+  rx[threadIdx.x] = fx;
+  ry[threadIdx.x] = fy;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < 256; ++i) {
+      sx += rx[i];
+      sy += ry[i];
+    }
+    const unsigned long long s = *p.step;
+    const long long r = (long long)(s % (unsigned long long)p.hist_cap);
+    p.hist[2 * r] = sx + p.fconst_x;
+    p.hist[2 * r + 1] = sy + p.fconst_y;
+    *p.step = s + 1;
+  }
+}
+
+// ---- moments (Eq. 4) of the stored f* for rows [y0, y0 + rows) ---------
+template <class S, class O>
+__global__ void fields_kernel(const S *__restrict__ A, StepParams p, O *__restrict__ rho, O *__restrict__ u,
+                              O *__restrict__ v, int y0, int rows) {
+  const long long n = (long long)rows * p.nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = y0 + (int)(i / p.nx);
+    const uint32_t lm = link_mask(p, x, y);
+    if (lm & LM_SOLID) {
+      rho[i] = (O)1;
+      u[i] = (O)0;
+      v[i] = (O)0;
+      continue;
+    }
+    const size_t o = (size_t)y * p.pitch + x;
+    double g[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = (double)Store<S>::ld(A[(size_t)k * p.plane + o]);
+    const double drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const double r = 1.0 + drho;
+    const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const double jy = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
+    rho[i] = (O)r;
+    u[i] = (O)(jx / r);
+    v[i] = (O)(jy / r);
+  }
+}
+
+// ---- per-row double sums of rho over fluid nodes (mass drift) ----------
+template <class S>
+__global__ void __launch_bounds__(256) mass_rows_kernel(const S *__restrict__ A, StepParams p, double *__restrict__ part,
+                                                        int y0) {
+  __shared__ double red[256];
+  const int y = y0 + blockIdx.x;
+  double acc = 0.0;
+  for (int x = threadIdx.x; x < p.nx; x += 256) {
+    if (link_mask(p, x, y) & LM_SOLID) continue;
+    const size_t o = (size_t)y * p.pitch + x;
+    double d = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d += (double)Store<S>::ld(A[(size_t)k * p.plane + o]);
+    acc += 1.0 + d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// ---- host-side launchers for one storage type ----------------------------
+template <class S>
+struct Launch {
+  static cudaError_t direct(const void *A, void *B, const StepParams &p, cudaStream_t st) {
+    const int nitems = p.ny * p.nseg;
+    step_direct<S, 256><<<nitems, 256, 0, st>>>((const S *)A, (S *)B, p);
+    return cudaGetLastError();
+  }
+
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t tma_one(int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    step_tma<S, NCW, CPT, STAGES><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    return cudaGetLastError();
+  }
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t tma_prep() {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  template <int NCW, int CPT, int STAGES>
+  static int tma_occ() {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma<S, NCW, CPT, STAGES>, (NCW + 1) * 32, smem) !=
+        cudaSuccess)
+      return 0;
+    return n;
+  }
+
+  static cudaError_t tma(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return tma_one<a, b, c>(grid, A, B, p, st);
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t prep(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return tma_prep<a, b, c>();
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+  static int occupancy(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return tma_occ<a, b, c>();
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return 0;
+  }
+  static size_t smem(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return tma_smem_bytes<S, a, b, c>();
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return 0;
+  }
+
+  static cudaError_t init(void *A, const StepParams &p, const double *r, const double *u, const double *v, int y0,
+                          int rows, cudaStream_t st) {
+    const long long n = (long long)rows * p.nx;
+    const int blocks = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    init_kernel<S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((S *)A, p, r, u, v, y0, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t force(const void *A, const StepParams &p, cudaStream_t st) {
+    force_kernel<S><<<1, 256, 0, st>>>((const S *)A, p);
+    return cudaGetLastError();
+  }
+  static cudaError_t fields(const void *A, const StepParams &p, void *r, void *u, void *v, int dbl, int y0, int rows,
+                            cudaStream_t st) {
+    const long long n = (long long)rows * p.nx;
+    const int blocks = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    if (dbl)
+      fields_kernel<S, double><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((const S *)A, p, (double *)r, (double *)u,
+                                                                        (double *)v, y0, rows);
+    else
+      fields_kernel<S, float><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((const S *)A, p, (float *)r, (float *)u,
+                                                                       (float *)v, y0, rows);
+    return cudaGetLastError();
+  }
+  static cudaError_t mass_rows(const void *A, const StepParams &p, double *part, int y0, int rows, cudaStream_t st) {
+    mass_rows_kernel<S><<<rows, 256, 0, st>>>((const S *)A, p, part, y0);
+    return cudaGetLastError();
+  }
+
+  static const KernelOps *table() {
+    static const KernelOps ops = {(int)sizeof(S), &direct, &tma, &prep, &occupancy, &smem, &init, &force, &fields,
+                                  &mass_rows};
+    return &ops;
+  }
+};
+
+}  // namespace gblbm

@@ -99,9 +99,12 @@ class Workload:
         v = np.zeros((self.ny, self.nx), np.float64)
         if self.perturb > 0.0:
             a = self.perturb * self.U
-            r = uniform01(self.seed, 2 * n)
-            u += (a * (2.0 * r[:n] - 1.0)).reshape(self.ny, self.nx)
-            v += (a * (2.0 * r[n:] - 1.0)).reshape(self.ny, self.nx)
+            uf, vf = u.reshape(-1), v.reshape(-1)
+            chunk = 1 << 24
+            for s in range(0, n, chunk):
+                m = min(chunk, n - s)
+                uf[s:s + m] += a * (2.0 * uniform01(self.seed, m, start=s) - 1.0)
+                vf[s:s + m] += a * (2.0 * uniform01(self.seed, m, start=n + s) - 1.0)
         solid = self.mask().astype(bool)
         u[solid] = 0.0
         v[solid] = 0.0
