@@ -238,8 +238,8 @@ def run_ours(args, workload):
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
     nx, ny = workload.nx, workload.ny
     stream = torch.cuda.Stream(device)
-    lat = lbm.lattice_for(workload, storage=storage, kernel=lbm.LBM_KERNEL_TMA if args.kernel == "tma"
-                          else lbm.LBM_KERNEL_DIRECT, shape=shape, ctas_per_sm=args.ctas_per_sm,
+    kernel = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "direct": lbm.LBM_KERNEL_DIRECT}[args.kernel]
+    lat = lbm.lattice_for(workload, storage=storage, kernel=kernel, shape=shape, ctas_per_sm=args.ctas_per_sm,
                           stream=stream, device=device)
     rho0, u0, v0 = workload.initial_fields()
     pin = [torch.from_numpy(a).pin_memory() for a in (rho0, u0, v0)]
@@ -337,9 +337,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default="f32")
-    ap.add_argument("--kernel", choices=["tma", "direct"], default="tma")
+    ap.add_argument("--kernel", choices=["auto", "tma", "direct"], default="auto")
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")
-    ap.add_argument("--ctas-per-sm", type=int, default=1)
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="0: the library's tuned default")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "production", "parity"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-rows", type=int, default=128)

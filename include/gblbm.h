@@ -53,14 +53,16 @@ extern "C" {
 #define LBM_BC_PERIODIC 1 /* Eq. 8: wrap in y */
 #define LBM_BC_ZOUHE 2    /* Eqs. 9-10: Zou-He velocity (U, 0) */
 
-/* ---- population storage ------------------------------------------------ */
-#define LBM_F32 0      /* float, stored as offsets f_i - w_i */
-#define LBM_F16_OFS 1  /* IEEE half offsets f_i - w_i, float arithmetic */
-#define LBM_BF16_OFS 2 /* bfloat16 offsets f_i - w_i, float arithmetic */
+/* ---- population storage ------------------------------------------------
+ * Populations are stored as offsets h_i = f_i - r_i from the free-stream
+ * equilibrium r_i = f_eq_i(rho = 1, u = (U, 0)) of Eq. 3. */
+#define LBM_F32 0      /* float offsets, float arithmetic */
+#define LBM_F16_OFS 1  /* IEEE half offsets, float arithmetic */
+#define LBM_BF16_OFS 2 /* bfloat16 offsets, float arithmetic */
 #define LBM_F64 3      /* double offsets, double arithmetic */
 
 /* ---- step kernel variants --------------------------------------------- */
-#define LBM_KERNEL_AUTO 0   /* the TMA-staged kernel with the tuned shape */
+#define LBM_KERNEL_AUTO 0   /* the tuned default for the storage type */
 #define LBM_KERNEL_DIRECT 1 /* one thread per cell, loads straight from HBM */
 #define LBM_KERNEL_TMA 2    /* persistent; bulk-async (TMA) row staging */
 
@@ -80,7 +82,7 @@ typedef struct lbm_opts {
   int consumer_warps;  /* TMA kernel: compute warps per CTA (0: tuned) */
   int cells_per_thread;/* TMA kernel: cells per compute thread per row tile */
   int stages;          /* TMA kernel: pipeline depth (row tiles in flight) */
-  int ctas_per_sm;     /* TMA kernel: resident CTAs per SM (0: 1) */
+  int ctas_per_sm;     /* TMA kernel: resident CTAs per SM (0: tuned default) */
   int graph_steps;     /* steps per captured CUDA graph (even); 0: auto; < 0: none */
   void *stream;        /* cudaStream_t to run on; NULL: the context makes its own */
   void *workspace;     /* device memory >= lbm_workspace_bytes(); NULL: the library allocates */
@@ -143,7 +145,7 @@ int lbm_fields_device(lbm_ctx *ctx, float *rho, float *u, float *v);
 /* Double-precision sum of rho over fluid nodes (mass-drift check). */
 int lbm_mass(lbm_ctx *ctx, double *mass);
 
-/* Checkpoint: the current f* as stored offsets f*_i - w_i, packed host
+/* Checkpoint: the current f* as stored offsets f*_i - r_i, packed host
  * [9][ny][nx] of the storage type (4, 2, 2 or 8 bytes per value).
  * bytes must equal 9 * nx * ny * element size. */
 int lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
@@ -163,6 +165,10 @@ int lbm_set_kernel(lbm_ctx *ctx, int kernel, int consumer_warps, int cells_per_t
 /* The kernel shape in use: kernel, consumer warps, cells/thread, stages,
  * CTAs per SM, grid size (CTAs) -- 6 ints. */
 int lbm_get_kernel(lbm_ctx *ctx, int *out6);
+
+/* The shapes the TMA kernel is built for: up to cap triples (compute warps,
+ * cells per thread, stages) into out; *count receives how many exist. */
+int lbm_kernel_shapes(int *out, int cap, int *count);
 
 /* The CUDA stream the context launches on (cudaStream_t). */
 int lbm_get_stream(lbm_ctx *ctx, void **stream);

@@ -1,0 +1,109 @@
+"""Autotuner for the step-kernel shape.
+
+For a lattice (or a batch of lattices) it times every candidate shape of the
+step kernel -- the persistent bulk-copy kernel with (compute warps, nodes per
+thread, pipeline stages) and resident CTAs per SM, plus the direct kernel --
+with CUDA events on the context's stream, and keeps the fastest.  Results are
+cached as JSON per (GPU name, lattice sizes, storage type) so a later run
+picks the shape without timing again.
+
+The cache lives in $GBLBM_TUNE_CACHE, else ~/.cache/gblbm/tune.json.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+DIRECT = "direct"
+
+
+def cache_path() -> str:
+    p = os.environ.get("GBLBM_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "gblbm", "tune.json")
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def cache_key(gpu_name: str, sizes, storage: int) -> str:
+    sz = ",".join(f"{nx}x{ny}" for nx, ny in sizes)
+    return f"{gpu_name}|s{storage}|{sz}"
+
+
+def candidates(ctas=(1, 2)):
+    from . import lbm
+    out = [(DIRECT, None, 1)]
+    for shp in lbm.lbm_kernel_shapes():
+        for c in ctas:
+            out.append(("tma", shp, c))
+    return out
+
+
+def time_candidate(target, cand, steps: int, warmup: int, stream) -> float:
+    """Milliseconds per step of `target` (an object with set_kernel/step/sync)
+    with candidate `cand`; inf if the shape does not fit."""
+    import torch
+    from . import lbm
+
+    kind, shape, ctas = cand
+    try:
+        if kind == DIRECT:
+            target.set_kernel(lbm.LBM_KERNEL_DIRECT)
+        else:
+            target.set_kernel(lbm.LBM_KERNEL_TMA, *shape, ctas_per_sm=ctas)
+    except lbm.LBMError:
+        return float("inf")
+    target.step(warmup)
+    target.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    target.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    target.sync()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune(target, sizes, storage: int, stream, steps: int = 20, warmup: int = 4, use_cache: bool = True,
+         ctas=(1, 2)):
+    """Pick the fastest step-kernel shape for `target`; returns a dict
+    {kind, shape, ctas_per_sm, ms_per_step, table} and applies it."""
+    import torch
+    from . import lbm
+
+    path = cache_path()
+    key = cache_key(torch.cuda.get_device_name(), sizes, storage)
+    data = _load(path) if use_cache else {}
+    best = data.get(key)
+    if best is None:
+        table = []
+        for cand in candidates(ctas):
+            ms = time_candidate(target, cand, steps, warmup, stream)
+            table.append({"kind": cand[0], "shape": cand[1], "ctas_per_sm": cand[2], "ms_per_step": ms})
+        fin = [t for t in table if t["ms_per_step"] != float("inf")]
+        best = dict(min(fin, key=lambda t: t["ms_per_step"]))
+        best["table"] = table
+        if use_cache:
+            data[key] = best
+            _save(path, data)
+    if best["kind"] == DIRECT:
+        target.set_kernel(lbm.LBM_KERNEL_DIRECT)
+    else:
+        target.set_kernel(lbm.LBM_KERNEL_TMA, *best["shape"], ctas_per_sm=best["ctas_per_sm"])
+    return best

@@ -45,8 +45,8 @@ int elem_size(int storage) {
 }
 
 // Host-side geometry: link map over the solid bounding box grown by one
-// node, the weight part of the Eq. 14 sum, and the bounding box of the
-// fluid nodes that own links.
+// node, the reference part (sum of 2 r_i c_i) of the Eq. 14 sum, and the
+// bounding box of the fluid nodes that own links.
 struct Geometry {
   int lx0 = 0, ly0 = 0, lw = 0, lh = 0;
   std::vector<uint16_t> lmap;
@@ -113,8 +113,8 @@ int build_geometry(const lbm_opts *o, const uint8_t *mask, Geometry *g) {
           g->fy1 = std::max(g->fy1, y);
           for (int d = 1; d < 9; ++d)
             if (m & (1u << OPP(d))) {  // d points into the solid
-              fcx += 2.0L * (long double)WD(d) * CX(d);
-              fcy += 2.0L * (long double)WD(d) * CY(d);
+              fcx += 2.0L * (long double)ref_pop(d, o->U) * CX(d);
+              fcy += 2.0L * (long double)ref_pop(d, o->U) * CY(d);
               ++g->links;
             }
         }
@@ -205,7 +205,13 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-int default_shape(int storage) { return storage == LBM_F64 ? 6 : 0; }
+// Defaults from the shape sweep on the 16000 x 8000 lattice: float storage
+// (12 compute warps, 2 nodes/thread, 4 stages, 1 CTA/SM) reaches ~95% of the
+// measured copy bandwidth; 16-bit storage the same shape at 2 CTAs/SM;
+// double storage is FP64-ALU bound and runs best on the direct kernel.
+int default_shape(int storage) { return storage == LBM_F64 ? 6 : 12; }
+int default_ctas(int storage) { return (storage == LBM_F16_OFS || storage == LBM_BF16_OFS) ? 2 : 1; }
+int default_kernel(int storage) { return storage == LBM_F64 ? LBM_KERNEL_DIRECT : LBM_KERNEL_TMA; }
 
 // Fill the step parameters for the chosen kernel shape (tile width, force
 // slots) and capture the multi-step graph.
@@ -402,15 +408,20 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.fconst_y = c->geo.fconst_y;
 
   int shape = default_shape(o->storage);
+  int kernel = o->kernel;
+  int ctas = o->ctas_per_sm > 0 ? o->ctas_per_sm : 1;
   if (o->consumer_warps || o->cells_per_thread || o->stages) {
     shape = -1;
     for (int s = 0; s < kNumTmaShapes; ++s)
       if (kTmaShapes[s].ncw == o->consumer_warps && kTmaShapes[s].cpt == o->cells_per_thread &&
           kTmaShapes[s].stages == o->stages)
         shape = s;
-    if (shape < 0 && o->kernel != LBM_KERNEL_DIRECT) return fail(LBM_ERR_ARG);
+    if (shape < 0 && kernel != LBM_KERNEL_DIRECT) return fail(LBM_ERR_ARG);
+  } else if (kernel == LBM_KERNEL_AUTO) {
+    kernel = default_kernel(o->storage);
+    if (o->ctas_per_sm <= 0) ctas = default_ctas(o->storage);
   }
-  rc = configure_kernel(c, o->kernel, std::max(shape, 0), o->ctas_per_sm > 0 ? o->ctas_per_sm : 1);
+  rc = configure_kernel(c, kernel, std::max(shape, 0), ctas);
   if (rc) return fail(rc);
   rc = capture_graph(c);
   if (rc) return fail(rc);
@@ -615,17 +626,21 @@ int lbm_set_populations(lbm_ctx *c, const void *src, size_t bytes, int64_t step)
 }
 
 int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int ctas_per_sm) {
-  if (!c) return LBM_ERR_ARG;
+  if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
   int shape = default_shape(c->o.storage);
+  int ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
   if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
     shape = -1;
     for (int s = 0; s < kNumTmaShapes; ++s)
       if (kTmaShapes[s].ncw == ncw && kTmaShapes[s].cpt == cpt && kTmaShapes[s].stages == stages) shape = s;
     if (shape < 0) return LBM_ERR_ARG;
+  } else if (kernel == LBM_KERNEL_AUTO) {
+    kernel = default_kernel(c->o.storage);
+    if (ctas_per_sm <= 0) ctas = default_ctas(c->o.storage);
   }
-  const int rc = configure_kernel(c, kernel, shape, ctas_per_sm > 0 ? ctas_per_sm : 1);
+  const int rc = configure_kernel(c, kernel, shape, ctas);
   if (rc) return rc;
   return capture_graph(c);
 }
@@ -639,6 +654,17 @@ int lbm_get_kernel(lbm_ctx *c, int *out6) {
   out6[3] = tma ? kTmaShapes[c->shape].stages : 0;
   out6[4] = tma ? c->ctas_per_sm : 0;
   out6[5] = c->grid;
+  return LBM_OK;
+}
+
+int lbm_kernel_shapes(int *out, int cap, int *count) {
+  if (!count || cap < 0 || (cap > 0 && !out)) return LBM_ERR_ARG;
+  *count = kNumTmaShapes;
+  for (int s = 0; s < kNumTmaShapes && s < cap; ++s) {
+    out[3 * s] = kTmaShapes[s].ncw;
+    out[3 * s + 1] = kTmaShapes[s].cpt;
+    out[3 * s + 2] = kTmaShapes[s].stages;
+  }
   return LBM_OK;
 }
 

@@ -1,12 +1,23 @@
 // lbm_device.cuh -- device building blocks of the fused D2Q9 step.
 //
-// Populations are stored as offsets g_i = f_i - w_i (Table 1 weights), in
-// the storage type S, in 9 planes [k][ny][pitch].  Arithmetic is float for
-// float/half/bfloat16 storage and double for double storage.  Working with
-// offsets keeps the stored magnitudes near |c_i.u| w_i instead of w_i, which
-// gives the 16-bit forms usable precision and the float form ~16x smaller
-// rounding steps; every rule below is linear in f with weight-symmetric
-// coefficients, so it reads the same on g.
+// Stored state.  Post-collision populations are kept as offsets from the
+// free-stream equilibrium, h_i = f_i - r_i with r_i = f_eq_i(rho = 1,
+// u = (U, 0)) of Eq. 3, in the storage type S, in 9 planes [k][ny][pitch].
+// Arithmetic is float for float/half/bfloat16 storage and double for double
+// storage.  In most of the lattice h is orders of magnitude smaller than f,
+// so rounding the stored value and every intermediate costs far less; the
+// rules below are the paper's rules rewritten on h (r satisfies each of them
+// exactly, so only constant corrections remain where a rule is not symmetric
+// in r -- the bounce-back of x-moving populations).
+//
+// Equilibrium in float.  The weights 1/9, 1/36 and the factors 1/3, 1/12 are
+// not representable in binary; multiplying by their float roundings biases
+// the momentum of f_eq by ~3e-8 of j at every node and step, a systematic
+// forcing that accumulates.  collide() therefore computes the diagonal
+// equilibria from Eq. 3, the axis pairs' even parts from Eq. 3, and their odd
+// parts and the rest population from exact mass and momentum balance --
+// identical in exact arithmetic, conservative to a few unbiased roundings in
+// float.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -24,6 +35,12 @@ __host__ __device__ constexpr double WD(int k) { return k == 0 ? 4.0 / 9.0 : (k 
 
 static_assert(OPP(1) == 3 && OPP(3) == 1 && OPP(2) == 4 && OPP(4) == 2, "opposites");
 static_assert(OPP(5) == 7 && OPP(7) == 5 && OPP(6) == 8 && OPP(8) == 6, "opposites");
+
+// Free-stream reference r_k = f_eq_k(1, (U, 0)) (Eq. 3), host and device.
+__host__ __device__ inline double ref_pop(int k, double U) {
+  const double cu = CX(k) * U;
+  return WD(k) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * U * U);
+}
 
 enum { BC_FREESLIP = 0, BC_PERIODIC = 1, BC_ZOUHE = 2 };
 
@@ -63,7 +80,7 @@ struct StepParams {
   int nx, ny, pitch, bc;
   long long plane;         // elements per population plane
   double omega;            // 1 / tau
-  double U;                // inlet / wall speed
+  double U;                // inlet / wall speed; also the reference velocity of h
   // link map over the region [lx0, lx0+lw) x [ly0, ly0+lh)
   const uint16_t *lmap;
   int lx0, ly0, lw, lh;
@@ -78,7 +95,7 @@ struct StepParams {
   unsigned long long *step;     // history entries written so far
   double *hist;                 // ring [cap][2] of (Fx, Fy)
   long long hist_cap;
-  double fconst_x, fconst_y;    // sum over links of 2 w_i c_i (offset part removed)
+  double fconst_x, fconst_y;    // sum over links of 2 r_i c_i (the reference part of Eq. 14)
 };
 
 __device__ __forceinline__ uint32_t link_mask(const StepParams &p, int x, int y) {
@@ -87,15 +104,28 @@ __device__ __forceinline__ uint32_t link_mask(const StepParams &p, int x, int y)
   return 0u;
 }
 
-// Pull (left side of Eq. 2) for the node (xe, y): g[k] = g*_k(xe - c_k).
-// A source outside the lattice yields the node's own g*_k (placeholder, later
+// True when no node of [xa, xb] in row y needs a boundary rule, a link-map
+// lookup or a bounds check: interior row, no inlet/outlet column, no overlap
+// with the link region.  Uniform over a warp's node chunk.
+__device__ __forceinline__ bool plain_span(const StepParams &p, int xa, int xb, int y) {
+  if (y < 1 || y > p.ny - 2 || xa < 1 || xb > p.nx - 2) return false;
+  const bool rows = (unsigned)(y - p.ly0) < (unsigned)p.lh;
+  const bool cols = xb >= p.lx0 && xa < p.lx0 + p.lw;
+  return !(rows && cols);
+}
+
+// Pull (left side of Eq. 2) for the node (xe, y): h[k] = h*_k(xe - c_k).
+// A source outside the lattice yields the node's own h*_k (placeholder, later
 // overwritten by a boundary rule); a solid source yields the node's own
-// g*_opp(k) (half-way bounce-back, reflected within the step).  Regular
-// sources come from fetch(k, sx) -- a staged row tile or HBM.
+// f*_opp(k), i.e. h*_opp(k) + r_opp(k) - r_k = h*_opp(k) - 6 w_k c_kx U
+// (half-way bounce-back, reflected within the step).  Regular sources come
+// from fetch(k, sx, sy) -- a staged row tile or HBM.
 template <class S, class Fetch>
 __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &p, int xe, int y, uint32_t lm,
-                                     Fetch fetch, typename Store<S>::C g[9]) {
+                                     Fetch fetch, typename Store<S>::C h[9]) {
+  using C = typename Store<S>::C;
   const size_t own = (size_t)y * p.pitch + xe;
+  const C U = (C)p.U;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int sx = xe - CX(k);
@@ -107,92 +137,107 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
       inside = inside && (unsigned)sy < (unsigned)p.ny;
     }
     if (!inside) {
-      g[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
+      h[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
     } else if (lm & (1u << k)) {
-      g[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
+      h[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
+      if (CX(k) != 0) h[k] += (C)(-6.0 * WD(k) * CX(k)) * U;
     } else {
-      g[k] = fetch(k, sx, sy);
+      h[k] = fetch(k, sx, sy);
     }
   }
 }
 
 // Boundary corrections after streaming (Section 2.3), in the order top row,
 // bottom row, inlet column.  The outlet (Eq. 13) is realised by computing
-// column nx-2 for column nx-1.  Every rule is written on offsets g = f - w;
-// the weights cancel because each rule pairs directions of equal weight and
-// the weights of each Zou-He density sum to one.
+// column nx-2 for column nx-1.  On h the free-slip and periodic copies are
+// unchanged (r is mirror-symmetric in y); in the Zou-He rules the density
+// becomes its deviation from 1, because r satisfies each rule with rho = 1.
 template <class C>
-__device__ __forceinline__ void boundaries(C g[9], int xe, int y, const StepParams &p) {
+__device__ __forceinline__ void boundaries(C h[9], int xe, int y, const StepParams &p) {
   const C U = (C)p.U;
   if (p.bc != BC_PERIODIC) {
     if (y == p.ny - 1) {
       if (p.bc == BC_FREESLIP) {  // Eq. 7a: f5 = f3, f8 = f7, f9 = f6
-        g[4] = g[2];
-        g[7] = g[6];
-        g[8] = g[5];
+        h[4] = h[2];
+        h[7] = h[6];
+        h[8] = h[5];
       } else {  // Eqs. 9a-c, rho_w = f1 + f2 + f4 + 2 (f3 + f6 + f7)
-        const C rho = (C)1 + (g[0] + g[1] + g[3] + (C)2 * (g[2] + g[5] + g[6]));
-        const C d = (C)0.5 * (g[1] - g[3]);
-        const C m = (C)0.5 * rho * U;
-        g[4] = g[2];
-        g[7] = g[5] + d - m;
-        g[8] = g[6] - d + m;
+        const C drho = h[0] + h[1] + h[3] + (C)2 * (h[2] + h[5] + h[6]);
+        const C d = (C)0.5 * (h[1] - h[3]);
+        const C m = (C)0.5 * drho * U;
+        h[4] = h[2];
+        h[7] = h[5] + d - m;
+        h[8] = h[6] - d + m;
       }
     } else if (y == 0) {
       if (p.bc == BC_FREESLIP) {  // Eq. 7b: f3 = f5, f7 = f8, f6 = f9
-        g[2] = g[4];
-        g[6] = g[7];
-        g[5] = g[8];
+        h[2] = h[4];
+        h[6] = h[7];
+        h[5] = h[8];
       } else {  // Eqs. 10a-c, rho_w = f1 + f2 + f4 + 2 (f5 + f8 + f9)
-        const C rho = (C)1 + (g[0] + g[1] + g[3] + (C)2 * (g[4] + g[7] + g[8]));
-        const C d = (C)0.5 * (g[1] - g[3]);
-        const C m = (C)0.5 * rho * U;
-        g[2] = g[4];
-        g[5] = g[7] - d + m;
-        g[6] = g[8] + d - m;
+        const C drho = h[0] + h[1] + h[3] + (C)2 * (h[4] + h[7] + h[8]);
+        const C d = (C)0.5 * (h[1] - h[3]);
+        const C m = (C)0.5 * drho * U;
+        h[2] = h[4];
+        h[5] = h[7] - d + m;
+        h[6] = h[8] + d - m;
       }
     }
   }
   if (xe == 0) {  // Zou-He velocity inlet (U, 0): unknowns f2, f6, f9
-    const C rho = ((C)1 + (g[0] + g[2] + g[4] + (C)2 * (g[3] + g[6] + g[7]))) / ((C)1 - U);
-    const C ru = rho * U;
-    const C h = (C)0.5 * (g[2] - g[4]);
-    g[1] = g[3] + ((C)2 / (C)3) * ru;
-    g[5] = g[7] - h + ru / (C)6;
-    g[8] = g[6] + h + ru / (C)6;
+    const C drho = (h[0] + h[2] + h[4] + (C)2 * (h[3] + h[6] + h[7])) / ((C)1 - U);
+    const C ru = drho * U;
+    const C hh = (C)0.5 * (h[2] - h[4]);
+    h[1] = h[3] + ((C)2 / (C)3) * ru;
+    h[5] = h[7] - hh + ru / (C)6;
+    h[8] = h[6] + hh + ru / (C)6;
   }
 }
 
-// BGK collision (Eq. 2) towards Eq. 3 with the moments of Eq. 4, on offsets:
-// delta_rho = sum g, rho u = sum g c, g_eq = w (delta_rho + rho (3 cu +
-// 9/2 cu^2 - 3/2 u.u)), g* = g + omega (g_eq - g).  Returns |u|^2.
+// BGK collision (Eq. 2) towards Eq. 3 with the moments of Eq. 4, on h.
+// delta_rho = sum h, j = (U, 0) + dj with dj = sum h c, and
+//   h_eq_k = w_k [delta_rho + 3 c.dj + (9/2 ((c.dj)(c.j + c.U) - delta_rho (c.U)^2)
+//            - 3/2 (dj.(j + U) - delta_rho U^2)) / rho],
+// which is f_eq_k(rho, j) - r_k written without cancellation.  Returns |u|^2.
 template <class C>
-__device__ __forceinline__ C collide(C g[9], C omega) {
-  const C drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-  const C rho = (C)1 + drho;
-  const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-  const C jy = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
-  const C inv = (C)1 / rho;
-  const C ux = jx * inv, uy = jy * inv;
-  const C uu = ux * ux + uy * uy;
-  const C base = drho - (C)1.5 * rho * uu;
+__device__ __forceinline__ C collide(C h[9], C omega, C U) {
+  const C drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const C djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  const C djy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+  const C jx = U + djx, jy = djy;
+  const C inv = (C)1 / ((C)1 + drho);
+  const C uu2 = drho * U * U;
+  const C q = (C)1.5 * ((djx * (jx + U) + djy * jy) - uu2) * inv;
+  C heq[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const C cu = (C)CX(k) * ux + (C)CY(k) * uy;
-    const C geq = (C)WD(k) * (base + rho * cu * ((C)3 + (C)4.5 * cu));
-    g[k] = g[k] + omega * (geq - g[k]);
+  for (int k = 5; k < 9; ++k) {
+    const C cdj = (C)CX(k) * djx + (C)CY(k) * djy;
+    const C cj = (C)CX(k) * jx + (C)CY(k) * jy;
+    const C cU = (C)CX(k) * U;
+    heq[k] = (C)(1.0 / 36.0) * (drho + (C)3 * cdj + ((C)4.5 * (cdj * (cj + cU) - uu2) * inv - q));
   }
-  return uu;
+  const C ex = (C)(2.0 / 9.0) * (drho + ((C)4.5 * (djx * (jx + U) - uu2) * inv - q));
+  const C ey = (C)(2.0 / 9.0) * (drho + ((C)4.5 * (djy * jy) * inv - q));
+  const C ox = djx - ((heq[5] - heq[6]) + (heq[8] - heq[7]));
+  const C oy = djy - ((heq[5] + heq[6]) - (heq[7] + heq[8]));
+  heq[1] = (C)0.5 * (ex + ox);
+  heq[3] = (C)0.5 * (ex - ox);
+  heq[2] = (C)0.5 * (ey + oy);
+  heq[4] = (C)0.5 * (ey - oy);
+  heq[0] = drho - (((heq[1] + heq[3]) + (heq[2] + heq[4])) + ((heq[5] + heq[6]) + (heq[7] + heq[8])));
+#pragma unroll
+  for (int k = 0; k < 9; ++k) h[k] = h[k] + omega * (heq[k] - h[k]);
+  return (jx * jx + jy * jy) * inv * inv;
 }
 
-// Offset part of the Eq. 14 link sum for one node: sum over directions i
-// pointing into the solid (bit opp(i) of the link mask) of 2 g*_i c_i.
+// h part of the Eq. 14 link sum for one node: sum over directions i pointing
+// into the solid (bit opp(i) of the link mask) of 2 h*_i c_i.
 template <class C>
-__device__ __forceinline__ void link_force(const C g[9], uint32_t lm, double &fx, double &fy) {
+__device__ __forceinline__ void link_force(const C h[9], uint32_t lm, double &fx, double &fy) {
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     if (lm & (1u << OPP(i))) {
-      const double v = 2.0 * (double)g[i];
+      const double v = 2.0 * (double)h[i];
       fx += v * CX(i);
       fy += v * CY(i);
     }

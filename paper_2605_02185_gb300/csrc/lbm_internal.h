@@ -41,7 +41,12 @@ const KernelOps *ops_f64();
   X(6, 8, 2, 4)             \
   X(7, 4, 2, 6)             \
   X(8, 8, 1, 4)             \
-  X(9, 4, 2, 4)
+  X(9, 4, 2, 4)             \
+  X(10, 8, 2, 3)            \
+  X(11, 16, 1, 4)           \
+  X(12, 12, 2, 4)           \
+  X(13, 16, 2, 2)           \
+  X(14, 4, 2, 3)
 
 struct TmaShape {
   int ncw, cpt, stages;

@@ -44,28 +44,46 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
   return y >= p.fy0 && y <= p.fy1 && s >= p.fs0 && s <= p.fs1;
 }
 
-// One node: pull, boundary rules, collision; stores g*(x) into B.
+// One node, general form: pull (with bounce-back and placeholders), boundary
+// rules, collision; stores h*(x) into B and adds the node's links to the force.
 template <class S, class Fetch>
 __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
-                                            int y, typename Store<S>::C omega, Fetch fetch, double &fx, double &fy,
-                                            bool &bad) {
+                                            int y, typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
+                                            double &fx, double &fy, bool &bad) {
   using C = typename Store<S>::C;
   const int xe = (x == p.nx - 1) ? p.nx - 2 : x;  // Eq. 13: outlet = column nx-2
   const uint32_t lm = link_mask(p, xe, y);
-  C g[9];
+  C h[9];
   if (lm & LM_SOLID) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = (C)0;
+    for (int k = 0; k < 9; ++k) h[k] = (C)0;
   } else {
-    pull<S>(A, p, xe, y, lm, fetch, g);
-    boundaries<C>(g, xe, y, p);
-    const C uu = collide<C>(g, omega);
+    pull<S>(A, p, xe, y, lm, fetch, h);
+    boundaries<C>(h, xe, y, p);
+    const C uu = collide<C>(h, omega, U);
     bad |= !(uu <= (C)0.09);
-    if ((lm & LM_LINKS) && x == xe) link_force<C>(g, lm, fx, fy);
+    if ((lm & LM_LINKS) && x == xe) link_force<C>(h, lm, fx, fy);
   }
-  const size_t o = (size_t)y * p.pitch + x;
+  S *o = B + (size_t)y * p.pitch + x;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) B[(size_t)k * p.plane + o] = Store<S>::st(g[k]);
+  for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
+}
+
+// One interior fluid node away from every boundary and link (plain_span):
+// every source is regular, no rule applies.
+template <class S, class Fetch>
+__device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams &p, int x, int y,
+                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
+                                             bool &bad) {
+  using C = typename Store<S>::C;
+  C h[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) h[k] = fetch(k, x - CX(k), y - CY(k));
+  const C uu = collide<C>(h, omega, U);
+  bad |= !(uu <= (C)0.09);
+  S *o = B + (size_t)y * p.pitch + x;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
 }
 
 // ---- direct kernel: one CTA per row tile, loads straight from HBM -------
@@ -78,13 +96,19 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   const int y = t / p.nseg, s = t - y * p.nseg;
   const int x0 = s * p.seg;
   const int x1 = min(x0 + p.seg, p.nx);
-  const C omega = (C)p.omega;
+  const C omega = (C)p.omega, U = (C)p.U;
   double fx = 0.0, fy = 0.0;
   bool bad = false;
   auto fetch = [&](int k, int sx, int sy) -> C {
     return Store<S>::ld(__ldg(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
   };
-  for (int x = x0 + (int)threadIdx.x; x < x1; x += NT) update_node<S>(A, B, p, x, y, omega, fetch, fx, fy, bad);
+  for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
+    const int x = xw + (int)(threadIdx.x & 31u);
+    if (plain_span(p, xw, xw + 31, y))
+      update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+    else if (x < x1)
+      update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+  }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))
     post_force<NT / 32>(p, y, s, fx, fy, (int)threadIdx.x, red, s_last, [] { __syncthreads(); });
@@ -176,7 +200,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
 
   // ---------------------------------------- compute warps
   const int ctid = threadIdx.x;
-  const C omega = (C)p.omega;
+  const C omega = (C)p.omega, U = (C)p.U;
   bool bad = false;
   int j = 0;
   for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
@@ -197,8 +221,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
       auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        const int x = x0 + c * NC + ctid;
-        if (x < p.nx) update_node<S>(A, B, p, x, y, omega, fetch, fx, fy, bad);
+        const int xw = x0 + c * NC + (ctid & ~31);
+        const int x = xw + lane;
+        if (plain_span(p, xw, xw + 31, y))
+          update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+        else if (x < p.nx)
+          update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
@@ -228,12 +256,12 @@ __global__ void init_kernel(S *__restrict__ A, StepParams p, const double *__res
       continue;
     }
     const double r = rho[i], ux = u[i], uy = v[i];
-    const double base = (r - 1.0) - 1.5 * r * (ux * ux + uy * uy);
+    const double uu = ux * ux + uy * uy;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double cu = CX(k) * ux + CY(k) * uy;
-      const double geq = WD(k) * (base + r * cu * (3.0 + 4.5 * cu));
-      A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)geq);
+      const double feq = WD(k) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+      A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)(feq - ref_pop(k, p.U)));
     }
   }
 }
@@ -294,7 +322,7 @@ __global__ void fields_kernel(const S *__restrict__ A, StepParams p, O *__restri
     for (int k = 0; k < 9; ++k) g[k] = (double)Store<S>::ld(A[(size_t)k * p.plane + o]);
     const double drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     const double r = 1.0 + drho;
-    const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const double jx = p.U + ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]));
     const double jy = (g[2] - g[4]) + (g[5] - g[8]) + (g[6] - g[7]);
     rho[i] = (O)r;
     u[i] = (O)(jx / r);

@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
         "lbm_get_window": (i, [vp, i, i, i, i, vp]),
         "lbm_set_kernel": (i, [vp, i, i, i, i, i]),
         "lbm_get_kernel": (i, [vp, vp]),
+        "lbm_kernel_shapes": (i, [vp, i, ctypes.POINTER(i)]),
         "lbm_get_stream": (i, [vp, ctypes.POINTER(vp)]),
         "lbm_launch_count": (i, [vp, ctypes.POINTER(i64)]),
         "lbm_bytes_per_step": (i, [vp, ctypes.POINTER(d)]),
@@ -262,6 +263,14 @@ def lbm_get_kernel(h) -> dict:
     return dict(zip(keys, (int(v) for v in out)))
 
 
+def lbm_kernel_shapes() -> list:
+    n = ctypes.c_int()
+    _check(load_library().lbm_kernel_shapes(None, 0, ctypes.byref(n)), "lbm_kernel_shapes")
+    out = np.zeros(3 * n.value, np.int32)
+    _check(load_library().lbm_kernel_shapes(_p(out), n.value, ctypes.byref(n)), "lbm_kernel_shapes")
+    return [tuple(int(v) for v in out[3 * i:3 * i + 3]) for i in range(n.value)]
+
+
 def lbm_get_stream(h) -> int:
     s = ctypes.c_void_p()
     _check(load_library().lbm_get_stream(h, ctypes.byref(s)), "lbm_get_stream")
@@ -289,7 +298,7 @@ class Lattice:
     """
 
     def __init__(self, nx, ny, tau, U, mask=None, bc=LBM_BC_FREESLIP, storage=LBM_F32, D_ref=0.0,
-                 rho_in=1.0, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=1, graph_steps=0,
+                 rho_in=1.0, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=0, graph_steps=0,
                  history_capacity=1 << 20, stream=None, device=None):
         import torch
 
@@ -374,7 +383,7 @@ class Lattice:
     def get_window(self, x0, y0, w, h) -> np.ndarray:
         return lbm_get_window(self.h, x0, y0, w, h, self.storage)
 
-    def set_kernel(self, kernel, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=1):
+    def set_kernel(self, kernel, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=0):
         lbm_set_kernel(self.h, kernel, consumer_warps, cells_per_thread, stages, ctas_per_sm)
 
     def kernel_info(self) -> dict:
