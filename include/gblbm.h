@@ -180,6 +180,32 @@ int lbm_launch_count(lbm_ctx *ctx, int64_t *count);
  * node (read f*(n-1), write f*(n)). */
 int lbm_bytes_per_step(lbm_ctx *ctx, double *bytes);
 
+/* One step WITHOUT ANY ALLOCATION, for callers that may not allocate device
+ * memory (their memory comes from a pool or arena they manage, or another
+ * runtime owns the allocator).  The paper has no counterpart: this is a
+ * service of the library.
+ *
+ * Reads f*(n) from f_in and writes f*(n+1) to f_out, both DEVICE buffers
+ * owned by the caller, packed [9][ny][nx] in the context's storage type as
+ * offsets from the free-stream equilibrium (the layout of
+ * lbm_get_populations), and writes the Eq. 14 force (Fx, Fy) of f*(n+1) to
+ * force_out, a DEVICE array of 2 doubles.  Geometry and parameters come from
+ * ctx; the context's own populations and history are neither read nor
+ * changed.  Runs the direct step kernel, asynchronously on the context
+ * stream.  f_in and f_out must not overlap.
+ *
+ * Scratch (force partials and reduction counters) lives in a 1 MiB device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits.  Bodies whose link-owning nodes span more than 65,520
+ * row tiles of 256 nodes are rejected with LBM_ERR_ARG.  The first call on a
+ * device looks up the array's address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call clears and reuses the
+ * same array: calls whose kernels overlap on the GPU (different streams, or
+ * several contexts) race on it.  The |u| > 0.3 stability check is not
+ * reported by this entry point.  No cudaMalloc, cudaFree or other
+ * allocating call is made. */
+int lbm_step_noalloc(lbm_ctx *ctx, const void *f_in, void *f_out, double *force_out);
+
 const char *lbm_error_string(int code);
 const char *lbm_version(void);
 

@@ -13,153 +13,12 @@
 #include "../../include/gblbm.h"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_ctx.h"
+#include "lbm_host.h"
 
 using namespace gblbm;
 
-namespace {
 
-constexpr size_t kAlign = 256;
-constexpr int kDirectThreads = 256;
-constexpr size_t kBandCells = size_t(1) << 20;  // staging band for init / fields
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-const KernelOps *ops_for(int storage) {
-  switch (storage) {
-    case LBM_F32: return ops_f32();
-    case LBM_F16_OFS: return ops_f16();
-    case LBM_BF16_OFS: return ops_bf16();
-    case LBM_F64: return ops_f64();
-  }
-  return nullptr;
-}
-
-int elem_size(int storage) {
-  switch (storage) {
-    case LBM_F32: return 4;
-    case LBM_F16_OFS: return 2;
-    case LBM_BF16_OFS: return 2;
-    case LBM_F64: return 8;
-  }
-  return 0;
-}
-
-// Host-side geometry: link map over the solid bounding box grown by one
-// node, the reference part (sum of 2 r_i c_i) of the Eq. 14 sum, and the
-// bounding box of the fluid nodes that own links.
-struct Geometry {
-  int lx0 = 0, ly0 = 0, lw = 0, lh = 0;
-  std::vector<uint16_t> lmap;
-  double fconst_x = 0.0, fconst_y = 0.0;
-  int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1;  // link-owning fluid nodes
-  int solid_rows = 0;
-  long long links = 0;
-};
-
-int check_opts(const lbm_opts *o) {
-  if (!o) return LBM_ERR_ARG;
-  if (o->nx < 5 || o->ny < 5) return LBM_ERR_ARG;
-  if ((long long)o->nx * o->ny > (1ll << 31) - 1) return LBM_ERR_ARG;
-  if (!(o->tau > 0.5) || !std::isfinite(o->tau)) return LBM_ERR_ARG;
-  if (!(o->U >= 0.0 && o->U < 0.3)) return LBM_ERR_ARG;
-  if (o->bc_top_bottom < LBM_BC_FREESLIP || o->bc_top_bottom > LBM_BC_ZOUHE) return LBM_ERR_ARG;
-  if (!elem_size(o->storage)) return LBM_ERR_ARG;
-  if (o->kernel < LBM_KERNEL_AUTO || o->kernel > LBM_KERNEL_TMA) return LBM_ERR_ARG;
-  return LBM_OK;
-}
-
-int build_geometry(const lbm_opts *o, const uint8_t *mask, Geometry *g) {
-  const int nx = o->nx, ny = o->ny;
-  int x0 = nx, x1 = -1, y0 = ny, y1 = -1;
-  if (mask) {
-    for (int y = 0; y < ny; ++y)
-      for (int x = 0; x < nx; ++x)
-        if (mask[(size_t)y * nx + x]) {
-          if (x < 2 || x > nx - 3 || y < 2 || y > ny - 3) return LBM_ERR_ARG;
-          x0 = std::min(x0, x);
-          x1 = std::max(x1, x);
-          y0 = std::min(y0, y);
-          y1 = std::max(y1, y);
-        }
-  }
-  if (x1 < 0) {  // no solid: an empty map
-    g->lx0 = g->ly0 = 0;
-    g->lw = g->lh = 0;
-    return LBM_OK;
-  }
-  g->solid_rows = y1 - y0 + 1;
-  g->lx0 = x0 - 1;
-  g->ly0 = y0 - 1;
-  g->lw = x1 - x0 + 3;
-  g->lh = y1 - y0 + 3;
-  g->lmap.assign((size_t)g->lw * g->lh, 0);
-  auto solid = [&](int x, int y) { return mask[(size_t)y * nx + x] != 0; };
-  long double fcx = 0.0L, fcy = 0.0L;
-  for (int j = 0; j < g->lh; ++j)
-    for (int i = 0; i < g->lw; ++i) {
-      const int x = g->lx0 + i, y = g->ly0 + j;
-      uint16_t m = 0;
-      if (solid(x, y)) {
-        m = (uint16_t)LM_SOLID;
-      } else {
-        for (int k = 1; k < 9; ++k) {
-          const int sx = x - CX(k), sy = y - CY(k);  // inside by the solid margin
-          if (solid(sx, sy)) m |= (uint16_t)(1u << k);
-        }
-        if (m) {
-          g->fx0 = g->fx1 < g->fx0 ? x : std::min(g->fx0, x);
-          g->fx1 = std::max(g->fx1, x);
-          g->fy0 = g->fy1 < g->fy0 ? y : std::min(g->fy0, y);
-          g->fy1 = std::max(g->fy1, y);
-          for (int d = 1; d < 9; ++d)
-            if (m & (1u << OPP(d))) {  // d points into the solid
-              fcx += 2.0L * (long double)ref_pop(d, o->U) * CX(d);
-              fcy += 2.0L * (long double)ref_pop(d, o->U) * CY(d);
-              ++g->links;
-            }
-        }
-      }
-      g->lmap[(size_t)j * g->lw + i] = m;
-    }
-  g->fconst_x = (double)fcx;
-  g->fconst_y = (double)fcy;
-  return LBM_OK;
-}
-
-}  // namespace
-
-struct lbm_ctx {
-  lbm_opts o{};
-  int dev = 0, sms = 0;
-  int nx = 0, ny = 0, pitch = 0, elem = 0;
-  long long plane = 0;
-  const KernelOps *ops = nullptr;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void *ws = nullptr;
-  size_t ws_bytes = 0;
-  bool own_ws = false;
-  void *buf[2] = {nullptr, nullptr};
-  int cur = 0;  // buf[cur] holds the current f*
-  uint16_t *lmap = nullptr;
-  double2 *slots = nullptr;
-  int slot_cap = 0;
-  double *hist = nullptr;
-  long long hist_cap = 0;
-  unsigned *ctrl = nullptr;  // [0] done, [1] err, [2..3] step counter
-  void *staging = nullptr;
-  size_t staging_bytes = 0;
-  int band_rows = 1;
-  Geometry geo;
-  double D_ref = 0.0, rho_in = 1.0;
-  bool inited = false;
-  long long launches = 0;
-  // step kernel
-  int kernel = LBM_KERNEL_TMA, shape = 0, ctas_per_sm = 1, grid = 0, seg = 0, nseg = 0;
-  StepParams p{};
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
-};
 
 namespace {
 
@@ -192,26 +51,6 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   *band_rows_out = band_rows;
   return off;
 }
-
-int cuda_fail(cudaError_t e) {
-  if (e == cudaSuccess) return LBM_OK;
-  if (e == cudaErrorMemoryAllocation) return LBM_ERR_OOM;
-  return LBM_ERR_CUDA;
-}
-
-#define CK(call)                                 \
-  do {                                           \
-    cudaError_t e_ = (call);                     \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
-  } while (0)
-
-// Defaults from the shape sweep on the 16000 x 8000 lattice: float storage
-// (12 compute warps, 2 nodes/thread, 4 stages, 1 CTA/SM) reaches ~95% of the
-// measured copy bandwidth; 16-bit storage the same shape at 2 CTAs/SM;
-// double storage is FP64-ALU bound and runs best on the direct kernel.
-int default_shape(int storage) { return storage == LBM_F64 ? 6 : 12; }
-int default_ctas(int storage) { return (storage == LBM_F16_OFS || storage == LBM_BF16_OFS) ? 2 : 1; }
-int default_kernel(int storage) { return storage == LBM_F64 ? LBM_KERNEL_DIRECT : LBM_KERNEL_TMA; }
 
 // Fill the step parameters for the chosen kernel shape (tile width, force
 // slots) and capture the multi-step graph.

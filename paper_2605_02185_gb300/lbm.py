@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "lbm_get_stream": (i, [vp, ctypes.POINTER(vp)]),
         "lbm_launch_count": (i, [vp, ctypes.POINTER(i64)]),
         "lbm_bytes_per_step": (i, [vp, ctypes.POINTER(d)]),
+        "lbm_step_noalloc": (i, [vp, vp, vp, vp]),
         "lbm_error_string": (ctypes.c_char_p, [i]),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -251,6 +252,12 @@ def lbm_get_window(h, x0: int, y0: int, w: int, hh: int, storage: int) -> np.nda
     return out
 
 
+def lbm_step_noalloc(h, f_in_ptr: int, f_out_ptr: int, force_out_ptr: int):
+    """One step from caller-owned device buffers, with no allocation (see gblbm.h)."""
+    _check(load_library().lbm_step_noalloc(h, ctypes.c_void_p(f_in_ptr), ctypes.c_void_p(f_out_ptr),
+                                           ctypes.c_void_p(force_out_ptr)), "lbm_step_noalloc")
+
+
 def lbm_set_kernel(h, kernel: int, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=1):
     _check(load_library().lbm_set_kernel(h, int(kernel), int(consumer_warps), int(cells_per_thread), int(stages),
                                          int(ctas_per_sm)), "lbm_set_kernel")
@@ -401,3 +408,4 @@ def lattice_for(workload, **kw) -> Lattice:
     kw.setdefault("bc", workload.bc)
     kw.setdefault("D_ref", float(workload.D))
     return Lattice(workload.nx, workload.ny, workload.tau, workload.U, mask=workload.mask(), **kw)
+
