@@ -206,6 +206,48 @@ int lbm_bytes_per_step(lbm_ctx *ctx, double *bytes);
  * allocating call is made. */
 int lbm_step_noalloc(lbm_ctx *ctx, const void *f_in, void *f_out, double *force_out);
 
+/* ---- batches of independent lattices --------------------------------------
+ * Many cylinder cases of different size and Reynolds number advanced by ONE
+ * step-kernel launch per step (the cases' row tiles are concatenated), with
+ * multi-step CUDA graphs.  Each case is a full lattice context; per-case
+ * reads (lbm_forces, lbm_fields, lbm_mass, lbm_get_populations, ...) use the
+ * context returned by lbm_batch_case.  Do not call lbm_step, lbm_init_fields,
+ * lbm_set_kernel or lbm_destroy on a case context: use the lbm_batch_*
+ * functions, which keep all cases on one step parity. */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct lbm_case {
+  int nx, ny;          /* lattice size of this case */
+  double tau, U;       /* relaxation time (Eq. 2) and inlet speed */
+  int bc_top_bottom;   /* LBM_BC_* */
+  const uint8_t *mask; /* host [ny][nx], 1 = solid (same rules as lbm_create), or NULL */
+  double D_ref;        /* Eq. 15 length; <= 0: (rows holding solid) - 1 */
+  double rho_in;       /* Eq. 15 density; <= 0: 1 */
+} lbm_case;
+
+/* Workspace bytes for these cases; common supplies storage, history
+ * capacity, kernel shape, graph steps (its nx, ny, tau, U, bc are ignored). */
+int lbm_batch_workspace_bytes(int ncases, const lbm_case *cases, const lbm_opts *common, size_t *bytes);
+/* Create the batch; common->stream / common->workspace as for lbm_create_ex. */
+int lbm_batch_create(int ncases, const lbm_case *cases, const lbm_opts *common, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *batch);
+/* The lattice context of case c (owned by the batch). */
+int lbm_batch_case(lbm_batch *batch, int c, lbm_ctx **ctx);
+/* Initial fields of case c (host double arrays, as lbm_init_fields). */
+int lbm_batch_init_fields(lbm_batch *batch, int c, const double *rho, const double *u, const double *v);
+/* Advance every case n steps (asynchronous); all cases must be initialised. */
+int lbm_batch_step(lbm_batch *batch, int64_t n);
+/* Wait; the worst error any case reported (LBM_ERR_TIMEOUT first). */
+int lbm_batch_sync(lbm_batch *batch);
+/* Kernel shape for the whole batch (as lbm_set_kernel); re-captures graphs. */
+int lbm_batch_set_kernel(lbm_batch *batch, int kernel, int consumer_warps, int cells_per_thread, int stages,
+                         int ctas_per_sm);
+int lbm_batch_get_kernel(lbm_batch *batch, int *out6);
+int lbm_batch_get_stream(lbm_batch *batch, void **stream);
+int lbm_batch_launch_count(lbm_batch *batch, int64_t *count);
+/* Total nodes of all cases, and the algorithmic HBM bytes of one batch step. */
+int lbm_batch_nodes(lbm_batch *batch, int64_t *nodes, double *bytes_per_step);
+
 const char *lbm_error_string(int code);
 const char *lbm_version(void);
 

@@ -130,6 +130,7 @@ int capture_graph(lbm_ctx *c) {
   err = cudaGraphInstantiate(&c->graph, graph, 0);
   cudaGraphDestroy(graph);
   CK(err);
+  CK(cudaGraphUpload(c->graph, c->stream));
   c->graph_steps = gs;
   return LBM_OK;
 }

@@ -98,6 +98,15 @@ struct StepParams {
   double fconst_x, fconst_y;    // sum over links of 2 r_i c_i (the reference part of Eq. 14)
 };
 
+// One lattice of a batch: its parameters, its two population buffers
+// (buf[parity] holds f*(n)) and the index of its first row tile in the
+// batch-wide tile numbering.
+struct CaseDesc {
+  StepParams p;
+  const void *buf[2];
+  long long item0;
+};
+
 __device__ __forceinline__ uint32_t link_mask(const StepParams &p, int x, int y) {
   unsigned dx = (unsigned)(x - p.lx0), dy = (unsigned)(y - p.ly0);
   if (dx < (unsigned)p.lw && dy < (unsigned)p.lh) return __ldg(p.lmap + (size_t)dy * p.lw + dx);

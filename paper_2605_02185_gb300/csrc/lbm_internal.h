@@ -8,6 +8,7 @@
 namespace gblbm {
 
 struct StepParams;
+struct CaseDesc;
 
 // Launchers of one storage type.  All launches are asynchronous on `st`.
 struct KernelOps {
@@ -23,6 +24,11 @@ struct KernelOps {
   cudaError_t (*fields)(const void *A, const StepParams &p, void *rho, void *u, void *v, int dbl, int y0, int rows,
                         cudaStream_t st);
   cudaError_t (*mass_rows)(const void *A, const StepParams &p, double *part, int y0, int rows, cudaStream_t st);
+  // batched step over the concatenated row tiles of `ncases` lattices
+  cudaError_t (*batch_direct)(const CaseDesc *cases, int ncases, long long nitems, int parity, cudaStream_t st);
+  cudaError_t (*batch_tma)(int shape, int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
+                           cudaStream_t st);
+  cudaError_t (*batch_prep)(int shape);
 };
 
 const KernelOps *ops_f32();

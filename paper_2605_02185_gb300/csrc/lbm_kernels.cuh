@@ -236,6 +236,187 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
 }
 
+// Case of batch-wide row tile t: the last case whose first tile is <= t.
+__device__ __forceinline__ int case_of(const CaseDesc *__restrict__ cases, int ncases, long long t) {
+  int lo = 0, hi = ncases - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&cases[mid].item0) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---- batched direct kernel: one CTA per row tile of any case ------------
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restrict__ cases, int ncases, int parity) {
+  using C = typename Store<S>::C;
+  __shared__ double red[2][NT / 32];
+  __shared__ int s_last;
+  const int c = case_of(cases, ncases, blockIdx.x);
+  const StepParams &p = cases[c].p;
+  const S *__restrict__ A = (const S *)cases[c].buf[parity];
+  S *__restrict__ B = (S *)cases[c].buf[parity ^ 1];
+  const int t = (int)(blockIdx.x - cases[c].item0);
+  const int y = t / p.nseg, s = t - y * p.nseg;
+  const int x0 = s * p.seg;
+  const int x1 = min(x0 + p.seg, p.nx);
+  const C omega = (C)p.omega, U = (C)p.U;
+  double fx = 0.0, fy = 0.0;
+  bool bad = false;
+  auto fetch = [&](int k, int sx, int sy) -> C {
+    return Store<S>::ld(__ldg(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
+  };
+  for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
+    const int x = xw + (int)(threadIdx.x & 31u);
+    if (plain_span(p, xw, xw + 31, y))
+      update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+    else if (x < x1)
+      update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
+  if (is_force_item(p, y, s))
+    post_force<NT / 32>(p, y, s, fx, fy, (int)threadIdx.x, red, s_last, [] { __syncthreads(); });
+}
+
+// ---- batched TMA kernel ---------------------------------------------------
+// The single-lattice pipeline over the concatenated row tiles of all cases:
+// the producer finds the case of each tile, stages its rows and passes
+// (case, row, tile) to the compute warps through a shared-memory slot of the
+// stage, published by the same mbarrier that counts the copied bytes.
+template <class S, int NCW, int CPT, int STAGES>
+__global__ void __launch_bounds__((NCW + 1) * 32)
+    step_tma_batch(const CaseDesc *__restrict__ cases, int ncases, long long nitems, int parity) {
+  using C = typename Store<S>::C;
+  constexpr int H = 16 / (int)sizeof(S);
+  constexpr int NC = NCW * 32;
+  constexpr int W = NC * CPT;
+  constexpr int SEG = W + 2 * H;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S *tiles = reinterpret_cast<S *>(smem);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
+  __shared__ int4 info[STAGES];
+  __shared__ double red[2][NCW];
+  __shared__ int s_last;
+  __shared__ int s_abort_store;
+  volatile int *s_abort = &s_abort_store;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(smem_addr(&bars[q]), 1);
+      mbar_init(smem_addr(&bars[STAGES + q]), NCW);
+    }
+    *s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NCW) {  // ---------------- producer
+    if (lane == 0) {
+      int j = 0;
+      for (long long t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+        const int st = j % STAGES;
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+          if (!*s_abort) atomicOr(cases[0].p.err, ERR_TIMEOUT);
+          *s_abort = 1;
+          break;
+        }
+        if (*s_abort) break;
+        const int c = case_of(cases, ncases, t);
+        const StepParams &p = cases[c].p;
+        const S *A = (const S *)cases[c].buf[parity];
+        const int tl = (int)(t - cases[c].item0);
+        const int y = tl / p.nseg, s = tl - y * p.nseg;
+        const int x0 = s * W;
+        const int xs = max(x0 - H, 0), xl = min(x0 + W + H, p.pitch);
+        const uint32_t bytes = (uint32_t)(xl - xs) * (uint32_t)sizeof(S);
+        int rows[9];
+        uint32_t total = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          int sy = y - CY(k);
+          if (p.bc == BC_PERIODIC) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+          rows[k] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
+          total += rows[k] >= 0 ? bytes : 0u;
+        }
+        info[st] = make_int4(c, y, s, 0);
+        const uint32_t fb = smem_addr(&bars[st]);
+        mbar_arrive_expect_tx(fb, total);
+        S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (rows[k] >= 0)
+            bulk_g2s(smem_addr(dst + (size_t)k * SEG), A + (size_t)k * p.plane + (size_t)rows[k] * p.pitch + xs, bytes,
+                     fb);
+      }
+      for (int q = max(0, j - STAGES); q < j; ++q) {
+        const uint32_t fb = smem_addr(&bars[q % STAGES]);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
+          if (global_ns() - t0 > 1000000000ull) {
+            atomicOr(cases[0].p.err, ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------------- compute warps
+  const int ctid = threadIdx.x;
+  int j = 0;
+  for (long long t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+    const int st = j % STAGES;
+    bool ok = false;
+    if (!*s_abort) {
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      if (!ok && !*s_abort) {
+        atomicOr(cases[0].p.err, ERR_TIMEOUT);
+        *s_abort = 1;
+      }
+    }
+    // the tile's case and row: from the stage slot, or (after an abort)
+    // recomputed so the force bookkeeping below stays uniform
+    int c, y, s;
+    if (ok) {
+      const int4 in = info[st];
+      c = in.x;
+      y = in.y;
+      s = in.z;
+    } else {
+      c = case_of(cases, ncases, t);
+      const int tl = (int)(t - cases[c].item0);
+      y = tl / cases[c].p.nseg;
+      s = tl - y * cases[c].p.nseg;
+    }
+    const StepParams &p = cases[c].p;
+    const S *__restrict__ A = (const S *)cases[c].buf[parity];
+    S *__restrict__ B = (S *)cases[c].buf[parity ^ 1];
+    const C omega = (C)p.omega, U = (C)p.U;
+    const int x0 = s * W;
+    double fx = 0.0, fy = 0.0;
+    bool bad = false;
+    if (ok) {
+      const S *tile = tiles + (size_t)st * 9 * SEG + (H - x0);
+      auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) {
+        const int xw = x0 + cc * NC + (ctid & ~31);
+        const int x = xw + lane;
+        if (plain_span(p, xw, xw + 31, y))
+          update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+        else if (x < p.nx)
+          update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+    if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
+  }
+}
+
 template <class S, int NCW, int CPT, int STAGES>
 constexpr size_t tma_smem_bytes() {
   return (size_t)STAGES * 9 * (NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t);
@@ -456,9 +637,51 @@ struct Launch {
     return cudaGetLastError();
   }
 
+  static cudaError_t batch_direct(const CaseDesc *cases, int ncases, long long nitems, int parity, cudaStream_t st) {
+    step_direct_batch<S, 256><<<(unsigned)nitems, 256, 0, st>>>(cases, ncases, parity);
+    return cudaGetLastError();
+  }
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t batch_tma_one(int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
+                                   cudaStream_t st) {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    step_tma_batch<S, NCW, CPT, STAGES><<<grid, (NCW + 1) * 32, smem, st>>>(cases, ncases, nitems, parity);
+    return cudaGetLastError();
+  }
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t batch_tma_prep() {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(step_tma_batch<S, NCW, CPT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  }
+  static cudaError_t batch_tma(int shape, int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
+                               cudaStream_t st) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return batch_tma_one<a, b, c>(grid, cases, ncases, nitems, parity, st);
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t batch_prep(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return batch_tma_prep<a, b, c>();
+      GBLBM_TMA_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static const KernelOps *table() {
-    static const KernelOps ops = {(int)sizeof(S), &direct, &tma, &prep, &occupancy, &smem, &init, &force, &fields,
-                                  &mass_rows};
+    static const KernelOps ops = {(int)sizeof(S), &direct,     &tma,          &prep,     &occupancy,
+                                  &smem,          &init,       &force,        &fields,   &mass_rows,
+                                  &batch_direct,  &batch_tma,  &batch_prep};
     return &ops;
   }
 };

@@ -50,6 +50,15 @@ class lbm_opts(ctypes.Structure):
     ]
 
 
+class lbm_case(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("tau", ctypes.c_double), ("U", ctypes.c_double),
+        ("bc_top_bottom", ctypes.c_int), ("mask", ctypes.c_void_p),
+        ("D_ref", ctypes.c_double), ("rho_in", ctypes.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -90,6 +99,18 @@ def load_library(path: str | None = None):
         "lbm_launch_count": (i, [vp, ctypes.POINTER(i64)]),
         "lbm_bytes_per_step": (i, [vp, ctypes.POINTER(d)]),
         "lbm_step_noalloc": (i, [vp, vp, vp, vp]),
+        "lbm_batch_workspace_bytes": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(sz)]),
+        "lbm_batch_create": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(vp)]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_case": (i, [vp, i, ctypes.POINTER(vp)]),
+        "lbm_batch_init_fields": (i, [vp, i, vp, vp, vp]),
+        "lbm_batch_step": (i, [vp, i64]),
+        "lbm_batch_sync": (i, [vp]),
+        "lbm_batch_set_kernel": (i, [vp, i, i, i, i, i]),
+        "lbm_batch_get_kernel": (i, [vp, vp]),
+        "lbm_batch_get_stream": (i, [vp, ctypes.POINTER(vp)]),
+        "lbm_batch_launch_count": (i, [vp, ctypes.POINTER(i64)]),
+        "lbm_batch_nodes": (i, [vp, ctypes.POINTER(i64), ctypes.POINTER(d)]),
         "lbm_error_string": (ctypes.c_char_p, [i]),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -409,3 +430,183 @@ def lattice_for(workload, **kw) -> Lattice:
     kw.setdefault("D_ref", float(workload.D))
     return Lattice(workload.nx, workload.ny, workload.tau, workload.U, mask=workload.mask(), **kw)
 
+
+def _case_array(cases, masks):
+    arr = (lbm_case * len(cases))()
+    for i, c in enumerate(cases):
+        arr[i].nx, arr[i].ny = int(c["nx"]), int(c["ny"])
+        arr[i].tau, arr[i].U = float(c["tau"]), float(c["U"])
+        arr[i].bc_top_bottom = int(c.get("bc", LBM_BC_FREESLIP))
+        arr[i].mask = masks[i].ctypes.data if masks[i] is not None else None
+        arr[i].D_ref = float(c.get("D_ref", 0.0))
+        arr[i].rho_in = float(c.get("rho_in", 1.0))
+    return arr
+
+
+def lbm_batch_workspace_bytes(cases, masks, opts: lbm_opts) -> int:
+    arr = _case_array(cases, masks)
+    out = ctypes.c_size_t()
+    _check(load_library().lbm_batch_workspace_bytes(len(cases), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(opts),
+                                                    ctypes.byref(out)), "lbm_batch_workspace_bytes")
+    return int(out.value)
+
+
+def lbm_batch_create(cases, masks, opts: lbm_opts):
+    arr = _case_array(cases, masks)
+    h = ctypes.c_void_p()
+    _check(load_library().lbm_batch_create(len(cases), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(opts),
+                                           ctypes.byref(h)), "lbm_batch_create")
+    return h
+
+
+def lbm_batch_destroy(h):
+    if h:
+        load_library().lbm_batch_destroy(h)
+
+
+def lbm_batch_case(h, c: int):
+    ctx = ctypes.c_void_p()
+    _check(load_library().lbm_batch_case(h, int(c), ctypes.byref(ctx)), "lbm_batch_case")
+    return ctx
+
+
+def lbm_batch_init_fields(h, c: int, rho, u, v):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, u, v)]
+    _check(load_library().lbm_batch_init_fields(h, int(c), *[_p(a) for a in arrs]), "lbm_batch_init_fields")
+
+
+def lbm_batch_step(h, n: int):
+    _check(load_library().lbm_batch_step(h, int(n)), "lbm_batch_step")
+
+
+def lbm_batch_sync(h):
+    _check(load_library().lbm_batch_sync(h), "lbm_batch_sync")
+
+
+def lbm_batch_set_kernel(h, kernel: int, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=0):
+    _check(load_library().lbm_batch_set_kernel(h, int(kernel), int(consumer_warps), int(cells_per_thread),
+                                               int(stages), int(ctas_per_sm)), "lbm_batch_set_kernel")
+
+
+def lbm_batch_get_kernel(h) -> dict:
+    out = np.zeros(6, np.int32)
+    _check(load_library().lbm_batch_get_kernel(h, _p(out)), "lbm_batch_get_kernel")
+    keys = ("kernel", "consumer_warps", "cells_per_thread", "stages", "ctas_per_sm", "grid")
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+def lbm_batch_launch_count(h) -> int:
+    c = ctypes.c_int64()
+    _check(load_library().lbm_batch_launch_count(h, ctypes.byref(c)), "lbm_batch_launch_count")
+    return int(c.value)
+
+
+def lbm_batch_nodes(h):
+    n = ctypes.c_int64()
+    b = ctypes.c_double()
+    _check(load_library().lbm_batch_nodes(h, ctypes.byref(n), ctypes.byref(b)), "lbm_batch_nodes")
+    return int(n.value), float(b.value)
+
+
+class Batch:
+    """Independent cylinder lattices advanced by one kernel launch per step.
+
+    ``cases`` is a list of ``workloads.Workload``.  Device memory is one
+    torch uint8 tensor; all cases run on one torch stream.
+    """
+
+    def __init__(self, cases, storage=LBM_F32, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=0,
+                 graph_steps=0, history_capacity=1 << 16, stream=None, device=None):
+        import torch
+
+        load_library()
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.workloads = list(cases)
+        self.masks = [np.ascontiguousarray(w.mask(), np.uint8) for w in self.workloads]
+        self.cases = [dict(nx=w.nx, ny=w.ny, tau=w.tau, U=w.U, bc=w.bc, D_ref=float(w.D)) for w in self.workloads]
+        o = lbm_opts_default()
+        o.storage = int(storage)
+        o.kernel = int(kernel)
+        if shape is not None:
+            o.consumer_warps, o.cells_per_thread, o.stages = (int(v) for v in shape)
+        o.ctas_per_sm = int(ctas_per_sm)
+        o.graph_steps = int(graph_steps)
+        o.history_capacity = int(history_capacity)
+        o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        nbytes = lbm_batch_workspace_bytes(self.cases, self.masks, o)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        o.workspace = ctypes.c_void_p(self.workspace.data_ptr())
+        o.workspace_bytes = nbytes
+        self.opts = o
+        self.storage = int(storage)
+        with torch.cuda.device(self.device):
+            self.h = lbm_batch_create(self.cases, self.masks, o)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.cases)
+
+    def init_fields(self, c, rho, u, v):
+        lbm_batch_init_fields(self.h, c, rho, u, v)
+
+    def init_all(self):
+        for c, w in enumerate(self.workloads):
+            self.init_fields(c, *w.initial_fields())
+
+    def step(self, n: int):
+        lbm_batch_step(self.h, n)
+
+    def sync(self):
+        lbm_batch_sync(self.h)
+
+    def case(self, c):
+        return lbm_batch_case(self.h, c)
+
+    def case_status(self, c) -> int:
+        """0, or the LBM_ERR_* code (e.g. LBM_ERR_UNSTABLE) case c reported."""
+        return int(load_library().lbm_sync(self.case(c)))
+
+    def forces_raw(self, c, first=0, n=None):
+        ctx = self.case(c)
+        if n is None:
+            n = lbm_force_count(ctx) - first
+        return lbm_forces_raw(ctx, first, n)
+
+    def forces(self, c, first=0, n=None):
+        ctx = self.case(c)
+        if n is None:
+            n = lbm_force_count(ctx) - first
+        return lbm_forces(ctx, first, n)
+
+    def fields(self, c, dtype=np.float64):
+        w = self.cases[c]
+        return lbm_fields(self.case(c), w["nx"], w["ny"], dtype)
+
+    def get_populations(self, c):
+        w = self.cases[c]
+        return lbm_get_populations(self.case(c), w["nx"], w["ny"], self.storage)
+
+    def set_kernel(self, kernel, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=0):
+        lbm_batch_set_kernel(self.h, kernel, consumer_warps, cells_per_thread, stages, ctas_per_sm)
+
+    def kernel_info(self) -> dict:
+        return lbm_batch_get_kernel(self.h)
+
+    def launch_count(self) -> int:
+        return lbm_batch_launch_count(self.h)
+
+    def nodes(self):
+        return lbm_batch_nodes(self.h)
