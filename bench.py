@@ -244,8 +244,9 @@ def run_ours(args, workload):
     nx, ny = workload.nx, workload.ny
     stream = torch.cuda.Stream(device)
     kernel = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "direct": lbm.LBM_KERNEL_DIRECT}[args.kernel]
+    coll = lbm.LBM_COLLIDE_MRT if args.collision == "mrt" else lbm.LBM_COLLIDE_BGK
     lat = lbm.lattice_for(workload, storage=storage, kernel=kernel, shape=shape, ctas_per_sm=args.ctas_per_sm,
-                          stream=stream, device=device)
+                          stream=stream, device=device, collision=coll)
     rho0, u0, v0 = workload.initial_fields()
     pin = [torch.from_numpy(a).pin_memory() for a in (rho0, u0, v0)]
     del rho0, u0, v0
@@ -318,6 +319,7 @@ def run_ours(args, workload):
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": workload.name, "nx": nx, "ny": ny, "D": workload.D, "U": workload.U,
                    "tau": workload.tau, "Re": workload.Re, "bc": "freeslip", "storage": args.storage + " offsets",
+                   "collision": args.collision,
                    "kernel": info, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"inputs {bytes_step / 2 / 1e9:.1f} GB of populations read per step, far above the "
                          "129 MB L2: no flush needed"},
@@ -349,7 +351,8 @@ def run_batch(args):
     dist_init("nccl")
     cases = W.batched_cases(args.cases, seed=4)
     stream = torch.cuda.Stream(device)
-    b = lbm.Batch(cases, stream=stream, device=device)
+    coll = lbm.LBM_COLLIDE_MRT if args.collision == "mrt" else lbm.LBM_COLLIDE_BGK
+    b = lbm.Batch(cases, stream=stream, device=device, collision=coll)
     b.init_all()
     tuned = None
     if args.tune:
@@ -382,7 +385,7 @@ def run_batch(args):
     # the same cases one after another, each a single graph-captured lattice
     t_seq = 0.0
     for w in cases:
-        lat = lbm.lattice_for(w, stream=stream, device=device)
+        lat = lbm.lattice_for(w, stream=stream, device=device, collision=coll)
         lat.init_fields(*w.initial_fields())
         lat.step(args.warmup)
         torch.cuda.synchronize(device)
@@ -407,6 +410,7 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch of {len(cases)} cylinder cases, Re in [60,200], D in {{20,30,40,60}}, "
                                    f"40D x 20D, U = 0.05, free-slip", "nodes": nodes, "kernel": info,
+                       "collision": args.collision,
                        "tuned": tuned},
             "sequential": {"value": seq, "unit": UNIT, "note": "same cases one after another, each a "
                                                                 "graph-captured single lattice"},
@@ -414,6 +418,34 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": src, "algorithmic_bytes_per_launch": bytes_step},
             "unstable_cases": unstable, "gpu_launches": int(launches), "clocks": clocks}), flush=True)
+    return 0
+
+
+def run_warmstart(args):
+    """Learned warm start (D = 40, 1600 x 800, Re in [60, 200]): train the
+    network on snapshots from the batched solver, then compare time to
+    periodic shedding of warm and cold starts on held-out Re."""
+    import torch
+    from paper_2605_02185_gb300 import warmstart as WS
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    cfg = WS.Config(snapshots=args.snapshots, train_cases=args.cases if args.cases != 64 else 32)
+    logs = []
+    net, info = WS.train(cfg, device, log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
+    rows, summary = WS.evaluate(net, cfg, n_eval=args.eval_cases, device=device,
+                                log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "wall time to periodic Cd/Cl/St, learned warm start vs cold start", "unit": "x faster",
+            "value": summary["median_time_speedup"], "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic", "dtype": "bf16 network, f32 lattice",
+            "config": {"workload": f"cylinder D = {cfg.D}, {40 * cfg.D} x {20 * cfg.D}, U = {cfg.U}, "
+                                   f"Re in [{cfg.re_lo}, {cfg.re_hi}], MRT collision", "train_cases": cfg.train_cases,
+                       "snapshots": info["snapshots"], "batch": cfg.batch},
+            "summary": summary, "train": {k: v for k, v in info.items() if k != "losses"},
+            "loss_first_last": [info["losses"][0], info["losses"][-1]], "cases": rows}), flush=True)
     return 0
 
 
@@ -425,9 +457,14 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default="f32")
     ap.add_argument("--kernel", choices=["auto", "tma", "direct"], default="auto")
+    ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
+                    help="bgk: Eq. 2 (the default hot path); mrt: the paper's Eq. 6 with its rates")
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="0: the library's tuned default")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "production", "parity", "batch"])
+    ap.add_argument("--workload", default="throughput",
+                    choices=["throughput", "production", "parity", "batch", "warmstart"])
+    ap.add_argument("--snapshots", type=int, default=20000, help="warmstart workload: training snapshots")
+    ap.add_argument("--eval-cases", type=int, default=16, help="warmstart workload: held-out Re values")
     ap.add_argument("--cases", type=int, default=64, help="batch workload: number of cases")
     ap.add_argument("--tune", action="store_true", help="batch workload: autotune the kernel shape first")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -439,6 +476,8 @@ def main(argv=None):
     from paper_2605_02185_gb300 import workloads as W
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     wl = {"throughput": W.THROUGHPUT_D400, "production": W.PRODUCTION_D80, "parity": W.PARITY_D10}[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -61,6 +61,10 @@ extern "C" {
 #define LBM_BF16_OFS 2 /* bfloat16 offsets, float arithmetic */
 #define LBM_F64 3      /* double offsets, double arithmetic */
 
+/* ---- collision model ---------------------------------------------------- */
+#define LBM_COLLIDE_BGK 0 /* Eq. 2: single relaxation time tau */
+#define LBM_COLLIDE_MRT 1 /* Eq. 6: M^-1 S M with S = diag[1, s_e, s_eps, 1, s_q, 1, s_q, 1/tau, 1/tau] */
+
 /* ---- step kernel variants --------------------------------------------- */
 #define LBM_KERNEL_AUTO 0   /* the tuned default for the storage type */
 #define LBM_KERNEL_DIRECT 1 /* one thread per cell, loads straight from HBM */
@@ -87,9 +91,13 @@ typedef struct lbm_opts {
   void *stream;        /* cudaStream_t to run on; NULL: the context makes its own */
   void *workspace;     /* device memory >= lbm_workspace_bytes(); NULL: the library allocates */
   size_t workspace_bytes;
+  int collision;       /* LBM_COLLIDE_BGK (Eq. 2) or LBM_COLLIDE_MRT (Eq. 6) */
+  double s_e, s_eps, s_q; /* MRT rates of the e, epsilon and q moments (paper: 1.1 each);
+                             the stress moments relax at 1/tau, rho and j are conserved */
 } lbm_opts;
 
-/* Defaults: F32 storage, auto kernel, free-slip, capacity 1 << 20. */
+/* Defaults: F32 storage, BGK, MRT rates 1.1, auto kernel, free-slip,
+ * capacity 1 << 20. */
 int lbm_opts_default(lbm_opts *opts);
 
 /* Bytes of device workspace lbm_create_ex needs for opts and this mask
@@ -111,6 +119,13 @@ void lbm_destroy(lbm_ctx *ctx);
  * arrays [ny][nx]), then the first collision, so the device holds f*(0), and
  * history entry 0 = the Eq. 14 force of f*(0).  Resets the history. */
 int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, const double *v);
+
+/* The same from DEVICE float arrays [ny][nx] (e.g. a network's prediction).
+ * with_noneq != 0 adds the first-order Chapman-Enskog non-equilibrium part
+ * f_neq_i = -(tau w_i rho / c_s^2) Q_i : grad u, Q_i = c_i c_i - c_s^2 I, with
+ * central differences (one-sided next to the lattice edge or the body), so
+ * the start carries the stresses of the given velocity field. */
+int lbm_init_fields_device(lbm_ctx *ctx, const float *rho, const float *u, const float *v, int with_noneq);
 
 /* Advance n >= 0 steps (asynchronous on the context stream).  Step n maps
  * f*(n-1) to f*(n) and appends the force of f*(n) to the history. */

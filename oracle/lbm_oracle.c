@@ -12,8 +12,8 @@
  * precision, compiled without FMA contraction.
  *
  * Readings of the paper taken here (the paper is silent or garbled on them):
- *   - Collision is BGK (Eq. 2) with the equilibrium of Eq. 3; MRT (Eq. 6) is
- *     not part of this oracle.
+ *   - Collision is BGK (Eq. 2) with the equilibrium of Eq. 3 unless the MRT
+ *     model (Eq. 6, below) is selected.
  *   - Streaming is written as a pull: f_i(x) = f*_i(x - c_i).  A source that
  *     is a solid node gives the half-way bounce-back value f*_opp(i)(x)
  *     (Section 2.4 and Section 3.1: reflected within the same time step).  A
@@ -35,6 +35,11 @@
  *   - Momentum exchange (Eq. 14): for a resting half-way wall
  *     f_in = f_out = f*_i(x), so each fluid-to-solid link (c_i pointing into
  *     the solid) adds 2 f*_i(x) c_i; the sum is the force on the solid.
+ *
+ * The paper's MRT collision (Eq. 6, with its S, m_eq and M) is available as
+ * the second collision model; its equilibrium moments are read as rho times
+ * the printed column (the printed column lacks the density factor) with
+ * j = rho u.
  *
  * A test-only Guo body force and a periodic x mode exist so that the oracle
  * can be pinned against closed forms (Poiseuille, Taylor-Green); they are not
@@ -59,9 +64,20 @@ static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 
 enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_WALLS = 3 };
 enum { ORC_X_INOUT = 0, ORC_X_PERIODIC = 1 };
 
+/* Eq. 6: the MRT transformation matrix M as printed (rows: rho, e, epsilon,
+ * j_x, q_x, j_y, q_y, p_xx, p_xy; columns: directions i = 1..9). */
+static const double MM[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},         {-4, -1, -1, -1, -1, 2, 2, 2, 2}, {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},      {0, -2, 0, 2, 0, 1, -1, -1, 1},   {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},      {0, 1, -1, 1, -1, 0, 0, 0, 0},    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+enum { ORC_BGK = 0, ORC_MRT = 1 };
+
 typedef struct {
   int nx, ny;
   int bc_y, bc_x;
+  int model;            /* ORC_BGK or ORC_MRT */
+  double s[9];          /* MRT relaxation rates, diagonal of S */
   double tau, U;
   double gx, gy;       /* test-only body force density (Guo forcing) */
   unsigned char *solid; /* [ny][nx], 1 = solid node */
@@ -148,6 +164,44 @@ void orc_collide_node(const double *f9, double tau, double gx, double gy, double
   }
 }
 
+void orc_mrt_matrix(double *m81) {
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) m81[9 * r + c] = MM[r][c];
+}
+
+/* Eq. 6 for one node: m = M f; m_eq = rho [1, -2 + 3 u.u, 1 - 3 u.u, u, -u, v,
+ * -v, u^2 - v^2, u v]; m* = m - S (m - m_eq); f* = M^-1 m*.  The rows of M are
+ * mutually orthogonal, so M^-1 = M^T diag(1 / |row_k|^2). */
+void orc_collide_node_mrt(const double *f9, const double *s, double *out9) {
+  double m[9], meq[9], rho, ux, uy;
+  orc_moments(f9, &rho, &ux, &uy);
+  for (int r = 0; r < 9; ++r) {
+    m[r] = 0.0;
+    for (int c = 0; c < 9; ++c) m[r] += MM[r][c] * f9[c];
+  }
+  double uu = ux * ux + uy * uy;
+  meq[0] = rho;
+  meq[1] = rho * (-2.0 + 3.0 * uu);
+  meq[2] = rho * (1.0 - 3.0 * uu);
+  meq[3] = rho * ux;
+  meq[4] = -rho * ux;
+  meq[5] = rho * uy;
+  meq[6] = -rho * uy;
+  meq[7] = rho * (ux * ux - uy * uy);
+  meq[8] = rho * ux * uy;
+  double ms[9];
+  for (int r = 0; r < 9; ++r) ms[r] = m[r] - s[r] * (m[r] - meq[r]);
+  for (int c = 0; c < 9; ++c) {
+    double acc = 0.0;
+    for (int r = 0; r < 9; ++r) {
+      double norm = 0.0;
+      for (int q = 0; q < 9; ++q) norm += MM[r][q] * MM[r][q];
+      acc += MM[r][c] * ms[r] / norm;
+    }
+    out9[c] = acc;
+  }
+}
+
 orc_t *orc_create(int nx, int ny, double tau, double U, int bc_y, int bc_x, const unsigned char *mask) {
   if (nx < 3 || ny < 3 || !(tau > 0.5)) return NULL;
   orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
@@ -158,6 +212,7 @@ orc_t *orc_create(int nx, int ny, double tau, double U, int bc_y, int bc_x, cons
   o->U = U;
   o->bc_y = bc_y;
   o->bc_x = bc_x;
+  o->model = ORC_BGK;
   size_t n = (size_t)nx * (size_t)ny;
   o->solid = (unsigned char *)calloc(n, 1);
   o->f = (double *)malloc(9 * n * sizeof(double));
@@ -188,6 +243,15 @@ void orc_destroy(orc_t *o) {
   free(o->fs);
   free(o->rowF);
   free(o);
+}
+
+/* Select the collision: ORC_BGK (Eq. 2) or ORC_MRT (Eq. 6) with the rates
+ * S = diag[1, s_e, s_eps, 1, s_q, 1, s_q, 1/tau, 1/tau] (the paper uses
+ * s_e = s_eps = s_q = 1.1). */
+void orc_set_collision(orc_t *o, int model, double s_e, double s_eps, double s_q) {
+  o->model = model;
+  const double s[9] = {1.0, s_e, s_eps, 1.0, s_q, 1.0, s_q, 1.0 / o->tau, 1.0 / o->tau};
+  for (int k = 0; k < 9; ++k) o->s[k] = s[k];
 }
 
 void orc_set_body_force(orc_t *o, double gx, double gy) {
@@ -224,7 +288,8 @@ static int neighbour(const orc_t *o, int x, int y, int k, int s, int *nxp, int *
   return 1;
 }
 
-/* Collision phase (Eq. 2, Eq. 3, Eq. 4) on every fluid node: f -> f*. */
+/* Collision phase (Eq. 2 or Eq. 6, with Eq. 3 and Eq. 4) on every fluid
+ * node: f -> f*. */
 void orc_collide(orc_t *o) {
   int nx = o->nx, ny = o->ny;
 #pragma omp parallel for schedule(static)
@@ -235,6 +300,8 @@ void orc_collide(orc_t *o) {
       for (int k = 0; k < 9; ++k) f9[k] = o->f[IDX(o, k, x, y)];
       if (o->solid[c])
         for (int k = 0; k < 9; ++k) out[k] = f9[k];
+      else if (o->model == ORC_MRT)
+        orc_collide_node_mrt(f9, o->s, out);
       else
         orc_collide_node(f9, o->tau, o->gx, o->gy, out);
       for (int k = 0; k < 9; ++k) o->fs[IDX(o, k, x, y)] = out[k];

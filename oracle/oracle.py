@@ -65,6 +65,9 @@ def _bind(lib):
     lib.orc_collide_node.argtypes = [p, d, d, d, p]
     lib.orc_constants.argtypes = [p, p, p, p]
     lib.orc_set_threads.argtypes = [i]
+    lib.orc_set_collision.argtypes = [p, i, d, d, d]
+    lib.orc_collide_node_mrt.argtypes = [p, p, p]
+    lib.orc_mrt_matrix.argtypes = [p]
     lib.orc_max_threads.restype = i
     return lib
 
@@ -120,6 +123,28 @@ def collide_node(f9, tau: float, gx: float = 0.0, gy: float = 0.0, lib=None) -> 
     return out
 
 
+BGK, MRT = 0, 1
+MRT_PAPER_RATES = (1.1, 1.1, 1.1)  # s_e, s_epsilon, s_q of the paper's S (Eq. 6)
+
+
+def mrt_matrix(lib=None) -> np.ndarray:
+    """M of Eq. 6 as the oracle holds it."""
+    lib = lib or load()
+    m = np.zeros(81, np.float64)
+    lib.orc_mrt_matrix(_ptr(m))
+    return m.reshape(9, 9)
+
+
+def collide_node_mrt(f9, s, lib=None) -> np.ndarray:
+    """Eq. 6 for one node with the rate vector s (diagonal of S)."""
+    lib = lib or load()
+    f9 = np.ascontiguousarray(f9, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    out = np.zeros(9, np.float64)
+    lib.orc_collide_node_mrt(_ptr(f9), _ptr(s), _ptr(out))
+    return out
+
+
 def set_threads(n: int, lib=None):
     (lib or load()).orc_set_threads(int(n))
 
@@ -153,6 +178,9 @@ class Oracle:
 
     def __del__(self):
         self.close()
+
+    def set_collision(self, model, s_e=1.1, s_eps=1.1, s_q=1.1):
+        self.lib.orc_set_collision(self.h, int(model), float(s_e), float(s_eps), float(s_q))
 
     def set_body_force(self, gx, gy):
         self.lib.orc_set_body_force(self.h, float(gx), float(gy))

@@ -148,6 +148,8 @@ int lbm_opts_default(lbm_opts *o) {
   o->history_capacity = 1ll << 20;
   o->kernel = LBM_KERNEL_AUTO;
   o->ctas_per_sm = 1;
+  o->collision = LBM_COLLIDE_BGK;
+  o->s_e = o->s_eps = o->s_q = 1.1;
   return LBM_OK;
 }
 
@@ -246,6 +248,10 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.hist_cap = c->hist_cap;
   p.fconst_x = c->geo.fconst_x;
   p.fconst_y = c->geo.fconst_y;
+  p.mrt = o->collision == LBM_COLLIDE_MRT ? 1 : 0;
+  p.s_e = o->s_e;
+  p.s_eps = o->s_eps;
+  p.s_q = o->s_q;
 
   int shape = default_shape(o->storage);
   int kernel = o->kernel;
@@ -304,6 +310,19 @@ int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u, const double
     CK(cudaMemcpyAsync(sv, v + off, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(c->ops->init(c->buf[0], c->p, sr, su, sv, y0, rows, c->stream));
   }
+  CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
+  CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
+  CK(c->ops->force(c->buf[0], c->p, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->inited = true;
+  return LBM_OK;
+}
+
+int lbm_init_fields_device(lbm_ctx *c, const float *rho, const float *u, const float *v, int with_noneq) {
+  if (!c || !rho || !u || !v) return LBM_ERR_ARG;
+  CK(cudaSetDevice(c->dev));
+  c->cur = 0;
+  CK(c->ops->init_device(c->buf[0], c->p, rho, u, v, with_noneq ? 1 : 0, 1.0 / c->p.omega, c->stream));
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
   CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
   CK(c->ops->force(c->buf[0], c->p, c->stream));

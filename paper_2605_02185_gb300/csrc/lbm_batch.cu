@@ -113,8 +113,9 @@ int configure_batch(lbm_batch *b, int kernel, int shape, int ctas) {
 cudaError_t launch_batch(lbm_batch *b, int parity) {
   const KernelOps *ops = b->cases[0]->ops;
   const int n = (int)b->cases.size();
-  if (b->kernel == LBM_KERNEL_DIRECT) return ops->batch_direct(b->desc, n, b->nitems, parity, b->stream);
-  return ops->batch_tma(b->shape, b->grid, b->desc, n, b->nitems, parity, b->stream);
+  const int mrt = b->common.collision == LBM_COLLIDE_MRT ? 1 : 0;
+  if (b->kernel == LBM_KERNEL_DIRECT) return ops->batch_direct(b->desc, n, b->nitems, parity, mrt, b->stream);
+  return ops->batch_tma(b->shape, b->grid, b->desc, n, b->nitems, parity, mrt, b->stream);
 }
 
 int capture_batch_graph(lbm_batch *b) {

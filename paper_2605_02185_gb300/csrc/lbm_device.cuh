@@ -96,6 +96,8 @@ struct StepParams {
   double *hist;                 // ring [cap][2] of (Fx, Fy)
   long long hist_cap;
   double fconst_x, fconst_y;    // sum over links of 2 r_i c_i (the reference part of Eq. 14)
+  int mrt;                      // 0: BGK (Eq. 2); 1: MRT (Eq. 6)
+  double s_e, s_eps, s_q;       // MRT rates of e, epsilon and q (the shear rate is omega)
 };
 
 // One lattice of a batch: its parameters, its two population buffers
@@ -237,6 +239,58 @@ __device__ __forceinline__ C collide(C h[9], C omega, C U) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = h[k] + omega * (heq[k] - h[k]);
   return (jx * jx + jy * jy) * inv * inv;
+}
+
+// MRT collision (Eq. 6) on h.  The moments of h use the integer rows of M;
+// the deviations d_k = m_k - m_eq_k of the non-conserved moments are formed
+// from small quantities only (Q = |j|^2/rho - U^2 without cancellation); the
+// update h* = h - M^T diag(s_k / |row_k|^2) d leaves rho and j untouched
+// exactly, because the conserved deviations are zero and M is integer.
+// Returns |u|^2.
+template <class C>
+__device__ __forceinline__ C collide_mrt(C h[9], C omega, C U, C se, C seps, C sq) {
+  const C drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const C djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+  const C djy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+  const C axis = (h[1] + h[2]) + (h[3] + h[4]);
+  const C diag = (h[5] + h[6]) + (h[7] + h[8]);
+  const C me = (C)2 * diag - axis - (C)4 * h[0];
+  const C meps = (C)4 * h[0] - (C)2 * axis + diag;
+  const C mqx = ((h[5] - h[6]) + (h[8] - h[7])) - (C)2 * (h[1] - h[3]);
+  const C mqy = ((h[5] + h[6]) - (h[7] + h[8])) - (C)2 * (h[2] - h[4]);
+  const C mpxx = (h[1] + h[3]) - (h[2] + h[4]);
+  const C mpxy = (h[5] - h[6]) + (h[7] - h[8]);
+  const C jx = U + djx, jy = djy;
+  const C inv = (C)1 / ((C)1 + drho);
+  const C uu2 = drho * U * U;
+  const C a = djx * (jx + U);
+  const C Q = ((a + djy * jy) - uu2) * inv;
+  const C ce = se * (C)(1.0 / 36.0) * ((me + (C)2 * drho) - (C)3 * Q);
+  const C cps = seps * (C)(1.0 / 36.0) * ((meps - drho) + (C)3 * Q);
+  const C cqx = sq * (C)(1.0 / 12.0) * (mqx + djx);
+  const C cqy = sq * (C)(1.0 / 12.0) * (mqy + djy);
+  const C cxx = omega * (C)0.25 * (mpxx - ((a - djy * jy) - uu2) * inv);
+  const C cxy = omega * (C)0.25 * (mpxy - jx * jy * inv);
+  const C ax = ce + (C)2 * cps;   // common part of the axis directions
+  const C dg = (C)2 * ce + cps;   // common part of the diagonals
+  h[0] -= (C)4 * (cps - ce);
+  h[1] -= ((C)(-2) * cqx + cxx) - ax;
+  h[2] -= ((C)(-2) * cqy - cxx) - ax;
+  h[3] -= ((C)2 * cqx + cxx) - ax;
+  h[4] -= ((C)2 * cqy - cxx) - ax;
+  h[5] -= dg + ((cqx + cqy) + cxy);
+  h[6] -= dg + ((cqy - cqx) - cxy);
+  h[7] -= dg - ((cqx + cqy) - cxy);
+  h[8] -= dg + ((cqx - cqy) - cxy);
+  return (jx * jx + jy * jy) * inv * inv;
+}
+
+// The collision of model MRT (0: BGK, 1: MRT), a compile-time choice so each
+// step kernel carries only its own collision.
+template <int MRT, class C>
+__device__ __forceinline__ C collide_model(C h[9], const StepParams &p, C omega, C U) {
+  if (MRT) return collide_mrt<C>(h, omega, U, (C)p.s_e, (C)p.s_eps, (C)p.s_q);
+  return collide<C>(h, omega, U);
 }
 
 // h part of the Eq. 14 link sum for one node: sum over directions i pointing

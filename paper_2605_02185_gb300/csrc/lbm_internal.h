@@ -25,10 +25,14 @@ struct KernelOps {
                         cudaStream_t st);
   cudaError_t (*mass_rows)(const void *A, const StepParams &p, double *part, int y0, int rows, cudaStream_t st);
   // batched step over the concatenated row tiles of `ncases` lattices
-  cudaError_t (*batch_direct)(const CaseDesc *cases, int ncases, long long nitems, int parity, cudaStream_t st);
+  cudaError_t (*batch_direct)(const CaseDesc *cases, int ncases, long long nitems, int parity, int mrt,
+                              cudaStream_t st);
   cudaError_t (*batch_tma)(int shape, int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
-                           cudaStream_t st);
+                           int mrt, cudaStream_t st);
   cudaError_t (*batch_prep)(int shape);
+  // initial state from device float fields, optionally with non-equilibrium part
+  cudaError_t (*init_device)(void *A, const StepParams &p, const float *rho, const float *u, const float *v,
+                             int with_noneq, double tau, cudaStream_t st);
 };
 
 const KernelOps *ops_f32();

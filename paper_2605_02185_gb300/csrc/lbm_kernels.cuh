@@ -46,7 +46,7 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
 
 // One node, general form: pull (with bounce-back and placeholders), boundary
 // rules, collision; stores h*(x) into B and adds the node's links to the force.
-template <class S, class Fetch>
+template <int MRT, class S, class Fetch>
 __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
                                             int y, typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
                                             double &fx, double &fy, bool &bad) {
@@ -60,7 +60,7 @@ __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restri
   } else {
     pull<S>(A, p, xe, y, lm, fetch, h);
     boundaries<C>(h, xe, y, p);
-    const C uu = collide<C>(h, omega, U);
+    const C uu = collide_model<MRT, C>(h, p, omega, U);
     bad |= !(uu <= (C)0.09);
     if ((lm & LM_LINKS) && x == xe) link_force<C>(h, lm, fx, fy);
   }
@@ -71,7 +71,7 @@ __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restri
 
 // One interior fluid node away from every boundary and link (plain_span):
 // every source is regular, no rule applies.
-template <class S, class Fetch>
+template <int MRT, class S, class Fetch>
 __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams &p, int x, int y,
                                              typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
                                              bool &bad) {
@@ -79,7 +79,7 @@ __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams
   C h[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = fetch(k, x - CX(k), y - CY(k));
-  const C uu = collide<C>(h, omega, U);
+  const C uu = collide_model<MRT, C>(h, p, omega, U);
   bad |= !(uu <= (C)0.09);
   S *o = B + (size_t)y * p.pitch + x;
 #pragma unroll
@@ -87,7 +87,7 @@ __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams
 }
 
 // ---- direct kernel: one CTA per row tile, loads straight from HBM -------
-template <class S, int NT>
+template <class S, int NT, int MRT>
 __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
   using C = typename Store<S>::C;
   __shared__ double red[2][NT / 32];
@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
     if (plain_span(p, xw, xw + 31, y))
-      update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+      update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
     else if (x < x1)
-      update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+      update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
 // (any x shift, no bank conflicts: consecutive lanes read consecutive
 // elements), apply the boundary rules, collide and store straight to HBM
 // with coalesced stores, then release the stage.  Every wait is bounded.
-template <class S, int NCW, int CPT, int STAGES>
+template <class S, int NCW, int CPT, int STAGES, int MRT>
 __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
   using C = typename Store<S>::C;
   constexpr int H = 16 / (int)sizeof(S);
@@ -224,9 +224,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
         const int xw = x0 + c * NC + (ctid & ~31);
         const int x = xw + lane;
         if (plain_span(p, xw, xw + 31, y))
-          update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+          update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
         else if (x < p.nx)
-          update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+          update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
@@ -248,7 +248,7 @@ __device__ __forceinline__ int case_of(const CaseDesc *__restrict__ cases, int n
 }
 
 // ---- batched direct kernel: one CTA per row tile of any case ------------
-template <class S, int NT>
+template <class S, int NT, int MRT>
 __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restrict__ cases, int ncases, int parity) {
   using C = typename Store<S>::C;
   __shared__ double red[2][NT / 32];
@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
     if (plain_span(p, xw, xw + 31, y))
-      update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+      update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
     else if (x < x1)
-      update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+      update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
 // the producer finds the case of each tile, stages its rows and passes
 // (case, row, tile) to the compute warps through a shared-memory slot of the
 // stage, published by the same mbarrier that counts the copied bytes.
-template <class S, int NCW, int CPT, int STAGES>
+template <class S, int NCW, int CPT, int STAGES, int MRT>
 __global__ void __launch_bounds__((NCW + 1) * 32)
     step_tma_batch(const CaseDesc *__restrict__ cases, int ncases, long long nitems, int parity) {
   using C = typename Store<S>::C;
@@ -405,9 +405,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         const int xw = x0 + cc * NC + (ctid & ~31);
         const int x = xw + lane;
         if (plain_span(p, xw, xw + 31, y))
-          update_plain<S>(B, p, x, y, omega, U, fetch, bad);
+          update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
         else if (x < p.nx)
-          update_node<S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+          update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
@@ -443,6 +443,64 @@ __global__ void init_kernel(S *__restrict__ A, StepParams p, const double *__res
       const double cu = CX(k) * ux + CY(k) * uy;
       const double feq = WD(k) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
       A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)(feq - ref_pop(k, p.U)));
+    }
+  }
+}
+
+// ---- initial state from DEVICE fields, optionally with the first-order
+// Chapman-Enskog non-equilibrium part (BGK, stress relaxation time tau):
+//   f_i = f_eq_i(rho, u) - (tau w_i rho / c_s^2) Q_i : grad u,
+//   Q_i = c_i c_i - c_s^2 I, c_s^2 = 1/3.
+// Velocity gradients: central differences, one-sided where a neighbour is
+// outside the lattice or solid, zero where both are.
+__device__ __forceinline__ bool fluid_at(const StepParams &p, int x, int y) {
+  if ((unsigned)x >= (unsigned)p.nx || (unsigned)y >= (unsigned)p.ny) return false;
+  return !(link_mask(p, x, y) & LM_SOLID);
+}
+__device__ __forceinline__ double diff1(const float *f, const StepParams &p, int x, int y, int ddx, int ddy) {
+  const bool lo = fluid_at(p, x - ddx, y - ddy), hi = fluid_at(p, x + ddx, y + ddy);
+  const size_t c = (size_t)y * p.nx + x;
+  const double fc = f[c];
+  const double fl = lo ? (double)f[(size_t)(y - ddy) * p.nx + (x - ddx)] : fc;
+  const double fh = hi ? (double)f[(size_t)(y + ddy) * p.nx + (x + ddx)] : fc;
+  if (lo && hi) return 0.5 * (fh - fl);
+  if (hi) return fh - fc;
+  if (lo) return fc - fl;
+  return 0.0;
+}
+
+template <class S>
+__global__ void init_device_kernel(S *__restrict__ A, StepParams p, const float *__restrict__ rho,
+                                   const float *__restrict__ u, const float *__restrict__ v, int with_noneq,
+                                   double tau) {
+  const long long n = (long long)p.nx * p.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.nx), y = (int)(i / p.nx);
+    const uint32_t lm = link_mask(p, x, y);
+    const size_t o = (size_t)y * p.pitch + x;
+    if (lm & LM_SOLID) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) A[(size_t)k * p.plane + o] = Store<S>::st(0);
+      continue;
+    }
+    const double r = rho[i], ux = u[i], uy = v[i];
+    const double uu = ux * ux + uy * uy;
+    double dudx = 0.0, dudy = 0.0, dvdx = 0.0, dvdy = 0.0;
+    if (with_noneq) {
+      dudx = diff1(u, p, x, y, 1, 0);
+      dudy = diff1(u, p, x, y, 0, 1);
+      dvdx = diff1(v, p, x, y, 1, 0);
+      dvdy = diff1(v, p, x, y, 0, 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double cu = CX(k) * ux + CY(k) * uy;
+      double f = WD(k) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+      if (with_noneq) {
+        const double qxx = CX(k) * CX(k) - 1.0 / 3.0, qyy = CY(k) * CY(k) - 1.0 / 3.0, qxy = CX(k) * CY(k);
+        f -= 3.0 * tau * WD(k) * r * (qxx * dudx + qyy * dvdy + qxy * (dudy + dvdx));
+      }
+      A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)(f - ref_pop(k, p.U)));
     }
   }
 }
@@ -540,7 +598,10 @@ template <class S>
 struct Launch {
   static cudaError_t direct(const void *A, void *B, const StepParams &p, cudaStream_t st) {
     const int nitems = p.ny * p.nseg;
-    step_direct<S, 256><<<nitems, 256, 0, st>>>((const S *)A, (S *)B, p);
+    if (p.mrt)
+      step_direct<S, 256, 1><<<nitems, 256, 0, st>>>((const S *)A, (S *)B, p);
+    else
+      step_direct<S, 256, 0><<<nitems, 256, 0, st>>>((const S *)A, (S *)B, p);
     return cudaGetLastError();
   }
 
@@ -548,24 +609,34 @@ struct Launch {
   static cudaError_t tma_one(int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
     constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    step_tma<S, NCW, CPT, STAGES><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    if (p.mrt)
+      step_tma<S, NCW, CPT, STAGES, 1><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    else
+      step_tma<S, NCW, CPT, STAGES, 0><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
     return cudaGetLastError();
   }
   template <int NCW, int CPT, int STAGES>
   static cudaError_t tma_prep() {
     constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    return cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES, 0>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
   }
   template <int NCW, int CPT, int STAGES>
   static int tma_occ() {
     constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
     if (smem > 227 * 1024) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma<S, NCW, CPT, STAGES>, (NCW + 1) * 32, smem) !=
-        cudaSuccess)
+    int m = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma<S, NCW, CPT, STAGES, 0>, (NCW + 1) * 32, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, step_tma<S, NCW, CPT, STAGES, 1>, (NCW + 1) * 32, smem) !=
+            cudaSuccess)
       return 0;
-    return n;
+    return n < m ? n : m;
   }
 
   static cudaError_t tma(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
@@ -616,6 +687,13 @@ struct Launch {
     init_kernel<S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((S *)A, p, r, u, v, y0, rows);
     return cudaGetLastError();
   }
+  static cudaError_t init_device(void *A, const StepParams &p, const float *r, const float *u, const float *v,
+                                 int with_noneq, double tau, cudaStream_t st) {
+    const long long n = (long long)p.nx * p.ny;
+    const int blocks = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    init_device_kernel<S><<<blocks > 0 ? blocks : 1, 256, 0, st>>>((S *)A, p, r, u, v, with_noneq, tau);
+    return cudaGetLastError();
+  }
   static cudaError_t force(const void *A, const StepParams &p, cudaStream_t st) {
     force_kernel<S><<<1, 256, 0, st>>>((const S *)A, p);
     return cudaGetLastError();
@@ -637,31 +715,41 @@ struct Launch {
     return cudaGetLastError();
   }
 
-  static cudaError_t batch_direct(const CaseDesc *cases, int ncases, long long nitems, int parity, cudaStream_t st) {
-    step_direct_batch<S, 256><<<(unsigned)nitems, 256, 0, st>>>(cases, ncases, parity);
+  static cudaError_t batch_direct(const CaseDesc *cases, int ncases, long long nitems, int parity, int mrt,
+                                  cudaStream_t st) {
+    if (mrt)
+      step_direct_batch<S, 256, 1><<<(unsigned)nitems, 256, 0, st>>>(cases, ncases, parity);
+    else
+      step_direct_batch<S, 256, 0><<<(unsigned)nitems, 256, 0, st>>>(cases, ncases, parity);
     return cudaGetLastError();
   }
   template <int NCW, int CPT, int STAGES>
   static cudaError_t batch_tma_one(int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
-                                   cudaStream_t st) {
+                                   int mrt, cudaStream_t st) {
     constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    step_tma_batch<S, NCW, CPT, STAGES><<<grid, (NCW + 1) * 32, smem, st>>>(cases, ncases, nitems, parity);
+    if (mrt)
+      step_tma_batch<S, NCW, CPT, STAGES, 1><<<grid, (NCW + 1) * 32, smem, st>>>(cases, ncases, nitems, parity);
+    else
+      step_tma_batch<S, NCW, CPT, STAGES, 0><<<grid, (NCW + 1) * 32, smem, st>>>(cases, ncases, nitems, parity);
     return cudaGetLastError();
   }
   template <int NCW, int CPT, int STAGES>
   static cudaError_t batch_tma_prep() {
     constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    return cudaFuncSetAttribute(step_tma_batch<S, NCW, CPT, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(step_tma_batch<S, NCW, CPT, STAGES, 0>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_tma_batch<S, NCW, CPT, STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem);
   }
   static cudaError_t batch_tma(int shape, int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
-                               cudaStream_t st) {
+                               int mrt, cudaStream_t st) {
     switch (shape) {
 #define X(id, a, b, c) \
   case id:             \
-    return batch_tma_one<a, b, c>(grid, cases, ncases, nitems, parity, st);
+    return batch_tma_one<a, b, c>(grid, cases, ncases, nitems, parity, mrt, st);
       GBLBM_TMA_SHAPES(X)
 #undef X
     }
@@ -681,7 +769,7 @@ struct Launch {
   static const KernelOps *table() {
     static const KernelOps ops = {(int)sizeof(S), &direct,     &tma,          &prep,     &occupancy,
                                   &smem,          &init,       &force,        &fields,   &mass_rows,
-                                  &batch_direct,  &batch_tma,  &batch_prep};
+                                  &batch_direct,  &batch_tma,  &batch_prep, &init_device};
     return &ops;
   }
 };

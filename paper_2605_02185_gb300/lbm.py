@@ -25,6 +25,7 @@ LBM_ERR_OOM, LBM_ERR_RANGE, LBM_ERR_STATE = -5, -6, -7
 LBM_BC_FREESLIP, LBM_BC_PERIODIC, LBM_BC_ZOUHE = 0, 1, 2
 LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64 = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA = 0, 1, 2
+LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
 ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8}
 ELEM_NUMPY = {LBM_F32: np.float32, LBM_F16_OFS: np.float16, LBM_BF16_OFS: np.uint16, LBM_F64: np.float64}
 
@@ -47,6 +48,8 @@ class lbm_opts(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int), ("graph_steps", ctypes.c_int),
         ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("collision", ctypes.c_int),
+        ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
     ]
 
 
@@ -80,6 +83,7 @@ def load_library(path: str | None = None):
         "lbm_create_ex": (i, [ctypes.POINTER(lbm_opts), vp, ctypes.POINTER(vp)]),
         "lbm_destroy": (None, [vp]),
         "lbm_init_fields": (i, [vp, vp, vp, vp]),
+        "lbm_init_fields_device": (i, [vp, vp, vp, vp, i]),
         "lbm_step": (i, [vp, i64]),
         "lbm_sync": (i, [vp]),
         "lbm_force_count": (i, [vp, ctypes.POINTER(i64)]),
@@ -192,6 +196,12 @@ def lbm_init_fields_ptr(h, rho_ptr: int, u_ptr: int, v_ptr: int):
     """Same as lbm_init_fields from raw host pointers (e.g. pinned tensors)."""
     _check(load_library().lbm_init_fields(h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr),
                                           ctypes.c_void_p(v_ptr)), "lbm_init_fields")
+
+
+def lbm_init_fields_device(h, rho_ptr: int, u_ptr: int, v_ptr: int, with_noneq: bool):
+    _check(load_library().lbm_init_fields_device(h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr),
+                                                 ctypes.c_void_p(v_ptr), int(bool(with_noneq))),
+           "lbm_init_fields_device")
 
 
 def lbm_step(h, n: int):
@@ -327,7 +337,8 @@ class Lattice:
 
     def __init__(self, nx, ny, tau, U, mask=None, bc=LBM_BC_FREESLIP, storage=LBM_F32, D_ref=0.0,
                  rho_in=1.0, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=0, graph_steps=0,
-                 history_capacity=1 << 20, stream=None, device=None):
+                 history_capacity=1 << 20, stream=None, device=None, collision=LBM_COLLIDE_BGK,
+                 mrt_rates=(1.1, 1.1, 1.1)):
         import torch
 
         load_library()
@@ -345,6 +356,8 @@ class Lattice:
             o.consumer_warps, o.cells_per_thread, o.stages = (int(v) for v in shape)
         o.ctas_per_sm = int(ctas_per_sm)
         o.graph_steps = int(graph_steps)
+        o.collision = int(collision)
+        o.s_e, o.s_eps, o.s_q = (float(v) for v in mrt_rates)
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         nbytes = lbm_workspace_bytes(o, mask)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -516,7 +529,8 @@ class Batch:
     """
 
     def __init__(self, cases, storage=LBM_F32, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=0,
-                 graph_steps=0, history_capacity=1 << 16, stream=None, device=None):
+                 graph_steps=0, history_capacity=1 << 16, stream=None, device=None, collision=LBM_COLLIDE_BGK,
+                 mrt_rates=(1.1, 1.1, 1.1)):
         import torch
 
         load_library()
@@ -534,6 +548,8 @@ class Batch:
         o.ctas_per_sm = int(ctas_per_sm)
         o.graph_steps = int(graph_steps)
         o.history_capacity = int(history_capacity)
+        o.collision = int(collision)
+        o.s_e, o.s_eps, o.s_q = (float(v) for v in mrt_rates)
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         nbytes = lbm_batch_workspace_bytes(self.cases, self.masks, o)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)

@@ -1,0 +1,283 @@
+"""Learned warm start of the cylinder solver.
+
+1. Snapshots.  A batch of cylinder cases at Re drawn log-uniformly from
+   [60, 200] (D = 40, U = 0.05 on the 40D x 20D box of the paper) runs in one
+   launch per step until every case sheds periodically; then the batch keeps
+   stepping and every round hands a few cases' fields (rho, u, v) to the
+   trainer, each labelled with its Re and its shedding phase (from the
+   upward zero crossings of its lift history).
+2. Training.  The encoder-decoder of ``nn.WarmStartNet`` learns
+   (mask, Re, phase) -> (rho, u, v) with Adam, entirely in the library's
+   BF16 tensor-core kernels.
+3. Warm start.  For a new Re the network predicts the field at phase 0; the
+   lattice starts from f_eq + f_neq(grad u) of that field.  The plain cold
+   start (uniform flow plus a small seeded perturbation) is both the fallback
+   and the judge: both runs go to periodic shedding (lift amplitude >= 0.05
+   changing by < 0.5 % per period for two consecutive periods) and the
+   prediction is rejected when its mean Cd, Cl amplitude or St differ from
+   the cold start's by more than 1 %.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import lbm, nn, postprocess
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Config:
+    D: int = 40
+    U: float = 0.05
+    re_lo: float = 60.0
+    re_hi: float = 200.0
+    train_cases: int = 32
+    snapshots: int = 20000
+    batch: int = 4
+    lr: float = 1e-3
+    lr_final: float = 1e-4
+    stride: int = 37          # solver steps between snapshot rounds
+    chunk: int = 1000         # steps between periodicity checks
+    spinup_max: int = 400_000
+    eval_max: int = 400_000
+    collision: int = lbm.LBM_COLLIDE_MRT
+    seed: int = 7
+    eval_seed: int = 11
+    perturb: float = 1e-3
+
+    @property
+    def rho_scale(self) -> float:
+        return self.U * self.U
+
+
+def re_values(n: int, seed: int, lo: float, hi: float) -> np.ndarray:
+    r = W.uniform01(seed, n)
+    return np.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * r)
+
+
+def re_feature(Re: float, cfg: Config) -> float:
+    return 2.0 * (math.log(Re) - math.log(cfg.re_lo)) / (math.log(cfg.re_hi) - math.log(cfg.re_lo)) - 1.0
+
+
+def case_for(Re: float, cfg: Config, seed: int) -> W.Workload:
+    return W.cylinder_case(cfg.D, cfg.U, Re, seed=seed, perturb=cfg.perturb, name=f"ws_D{cfg.D}_Re{Re:.1f}")
+
+
+def phase_now(cl: np.ndarray) -> float | None:
+    """Shedding phase in [0, 2 pi) at the last history entry: the time since
+    the last upward zero crossing of Cl over the last period."""
+    z = postprocess.upward_crossings(cl)
+    if len(z) < 2:
+        return None
+    T = z[-1] - z[-2]
+    return float((2 * math.pi * (len(cl) - 1 - z[-1]) / T) % (2 * math.pi))
+
+
+class History:
+    """Host copy of a context's Cd/Cl history, fetched incrementally."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.cd = np.zeros(0)
+        self.cl = np.zeros(0)
+
+    def update(self):
+        n = lbm.lbm_force_count(self.ctx)
+        have = len(self.cd)
+        if n > have:
+            cd, cl = lbm.lbm_forces(self.ctx, have, n - have)
+            self.cd = np.concatenate([self.cd, cd])
+            self.cl = np.concatenate([self.cl, cl])
+        return self.cd, self.cl
+
+
+# ------------------------------------------------------------------ data
+
+
+class SnapshotSource:
+    """Training cases advanced together; yields labelled snapshots."""
+
+    def __init__(self, cfg: Config, device, stream):
+        import torch
+        self.cfg = cfg
+        self.res = re_values(cfg.train_cases, cfg.seed, cfg.re_lo, cfg.re_hi)
+        self.cases = [case_for(Re, cfg, cfg.seed * 1000 + i) for i, Re in enumerate(self.res)]
+        self.batch = lbm.Batch(self.cases, collision=cfg.collision, stream=stream, device=device,
+                               history_capacity=1 << 20)
+        self.batch.init_all()
+        wl = self.cases[0]
+        self.H, self.W = wl.ny, wl.nx
+        self.solid = torch.from_numpy(wl.mask()).to(device)
+        self.periodic = []
+        self.steps = 0
+        self.hist = [History(self.batch.case(c)) for c in range(len(self.cases))]
+
+    def spin_up(self, log=print):
+        cfg = self.cfg
+        done = [None] * len(self.cases)
+        while self.steps < cfg.spinup_max and any(d is None for d in done):
+            self.batch.step(cfg.chunk)
+            self.steps += cfg.chunk
+            for c in range(len(self.cases)):
+                if done[c] is None:
+                    _, cl = self.hist[c].update()
+                    i = postprocess.periodic_index(cl)
+                    if i is not None:
+                        done[c] = i
+        self.periodic = [c for c in range(len(self.cases)) if done[c] is not None]
+        log(f"spin-up: {self.steps} steps, {len(self.periodic)}/{len(self.cases)} cases periodic")
+        return done
+
+    def phase(self, c: int) -> float:
+        _, cl = self.hist[c].update()
+        ph = phase_now(cl[-40000:])
+        return 0.0 if ph is None else ph
+
+
+# ----------------------------------------------------------------- train
+
+
+def train(cfg: Config, device=None, log=print):
+    """Generate snapshots with the batched solver and train the network.
+    Returns (net, info)."""
+    import torch
+    device = device or torch.device("cuda")
+    stream = torch.cuda.Stream(device)
+    src = SnapshotSource(cfg, device, stream)
+    t0 = time.perf_counter()
+    src.spin_up(log)
+    t_spin = time.perf_counter() - t0
+    H, Wd, B = src.H, src.W, cfg.batch
+    net = nn.WarmStartNet(B, H, Wd, device, seed=cfg.seed)
+    P1 = H * Wd
+    target = torch.empty((B * P1, 3), dtype=torch.float32, device=device)
+    weight = torch.empty(B * P1, dtype=torch.float32, device=device)
+    fr = [torch.empty((H, Wd), dtype=torch.float32, device=device) for _ in range(3)]
+    iters = max(1, cfg.snapshots // B)
+    cases = src.periodic or list(range(len(src.cases)))
+    losses = []
+    t1 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for it in range(iters):
+            src.batch.step(cfg.stride)
+            src.steps += cfg.stride
+            for j in range(B):
+                c = cases[(it * B + j) % len(cases)]
+                ctx = src.batch.case(c)
+                lbm.lbm_fields_device(ctx, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr())
+                nn.encode_target(fr[0], fr[1], fr[2], src.solid, P1, cfg.U, cfg.rho_scale, target[j * P1:(j + 1) * P1],
+                                 weight[j * P1:(j + 1) * P1], stream)
+                nn.encode_input(src.solid, re_feature(float(src.res[c]), cfg), src.phase(c), H, Wd, net.x0[j], stream)
+            net.forward(stream)
+            loss = net.loss_and_grad(target, weight, stream)
+            net.backward(stream)
+            frac = it / max(iters - 1, 1)
+            lr = cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1 + math.cos(math.pi * frac))
+            net.adam_step(lr, stream)
+            if it % 50 == 0 or it == iters - 1:
+                stream.synchronize()
+                losses.append((it, loss.item()))
+                if it % 500 == 0:
+                    log(f"iter {it}/{iters} loss {loss.item():.4e}")
+    stream.synchronize()
+    t_train = time.perf_counter() - t1
+    info = {"spinup_s": t_spin, "train_s": t_train, "iters": iters, "snapshots": iters * B,
+            "train_re": [float(r) for r in src.res], "periodic_cases": len(src.periodic),
+            "losses": losses, "flops_per_sample_fwd": net.flops_per_sample()}
+    src.batch.close()
+    return net, info
+
+
+# -------------------------------------------------------------- evaluate
+
+
+def predictor(net: nn.WarmStartNet, device):
+    """A one-sample network sharing the trained layers."""
+    p = nn.WarmStartNet(1, net.H, net.W, device)
+    p.layers = net.layers
+    return p
+
+
+def run_to_periodic(lat, wl: W.Workload, max_steps: int, chunk: int):
+    """Step until the lift is periodic; returns (steps at detection, stats)."""
+    steps = 0
+    hist = History(lat.h)
+    while steps < max_steps:
+        lat.step(chunk)
+        steps += chunk
+        cd, cl = hist.update()
+        i = postprocess.periodic_index(cl)
+        if i is not None:
+            st = postprocess.statistics(cd[:i + 1], cl[:i + 1], wl.D, wl.U, periods=2)
+            return i, st
+    return None, None
+
+
+def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: int):
+    import torch
+    wl = case_for(Re, cfg, seed)
+    stream = torch.cuda.Stream(device)
+    out = {"Re": float(Re)}
+    # cold start: uniform flow plus the seeded perturbation
+    lat = lbm.lattice_for(wl, collision=cfg.collision, stream=stream, device=device)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    lat.init_fields(*wl.initial_fields())
+    n_cold, st_cold = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk)
+    lat.sync()
+    out["cold"] = {"steps": n_cold, "wall_s": time.perf_counter() - t0, **(st_cold or {})}
+    lat.close()
+    # warm start: network prediction at phase 0, f_eq + f_neq
+    lat = lbm.lattice_for(wl, collision=cfg.collision, stream=stream, device=device)
+    solid = torch.from_numpy(wl.mask()).to(device)
+    fr = [torch.empty((wl.ny, wl.nx), dtype=torch.float32, device=device) for _ in range(3)]
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        nn.encode_input(solid, re_feature(Re, cfg), 0.0, wl.ny, wl.nx, pred.x0[0], stream)
+        pred.forward(stream)
+        nn.decode_output(pred.out, pred.OUT_C, solid, wl.nx * wl.ny, cfg.U, cfg.rho_scale, fr[0], fr[1], fr[2], stream)
+    stream.synchronize()
+    t_inf = time.perf_counter() - t0
+    lbm.lbm_init_fields_device(lat.h, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr(), True)
+    n_warm, st_warm = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk)
+    lat.sync()
+    out["warm"] = {"steps": n_warm, "wall_s": time.perf_counter() - t0, "inference_s": t_inf, **(st_warm or {})}
+    lat.close()
+    if st_cold and st_warm:
+        d = {k: abs(st_warm[k] - st_cold[k]) / abs(st_cold[k]) for k in ("cd_mean", "cl_amp", "st")}
+        out["drift"] = d
+        out["accepted"] = all(v <= 0.01 for v in d.values())
+        out["step_speedup"] = n_cold / max(n_warm, 1)
+        out["time_speedup"] = out["cold"]["wall_s"] / out["warm"]["wall_s"]
+    else:
+        out["accepted"] = False
+    return out
+
+
+def evaluate(net, cfg: Config, n_eval: int = 16, device=None, log=print):
+    import torch
+    device = device or torch.device("cuda")
+    pred = predictor(net, device)
+    res = re_values(n_eval, cfg.eval_seed, cfg.re_lo, cfg.re_hi)
+    rows = []
+    for i, Re in enumerate(res):
+        r = evaluate_case(pred, float(Re), cfg, device, seed=cfg.eval_seed * 1000 + i)
+        log(f"Re {Re:.1f}: cold {r['cold'].get('steps')} steps {r['cold']['wall_s']:.2f}s, "
+            f"warm {r['warm'].get('steps')} steps {r['warm']['wall_s']:.2f}s, accepted {r['accepted']}, "
+            f"drift {r.get('drift')}")
+        rows.append(r)
+    acc = [r for r in rows if r["accepted"]]
+    summary = {
+        "cases": len(rows), "accepted": len(acc),
+        "median_step_speedup": float(np.median([r["step_speedup"] for r in acc])) if acc else None,
+        "median_time_speedup": float(np.median([r["time_speedup"] for r in acc])) if acc else None,
+        "total_time_speedup": (sum(r["cold"]["wall_s"] for r in rows) /
+                               sum(r["warm"]["wall_s"] if r["accepted"] else r["warm"]["wall_s"] + r["cold"]["wall_s"]
+                                   for r in rows)),
+    }
+    return rows, summary

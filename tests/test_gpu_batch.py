@@ -85,7 +85,7 @@ def test_batch_of_paper_boxes_and_autotune(tmp_path, monkeypatch):
     from paper_2605_02185_gb300 import autotune
     monkeypatch.setenv("GBLBM_TUNE_CACHE", str(tmp_path / "tune.json"))
     cases = W.batched_cases(6, seed=4)
-    b = lbm.Batch(cases)
+    b = lbm.Batch(cases, collision=lbm.LBM_COLLIDE_MRT)  # MRT keeps the low-tau cases stable
     b.init_all()
     nodes, bytes_step = b.nodes()
     assert nodes == sum(w.nx * w.ny for w in cases)
@@ -94,11 +94,13 @@ def test_batch_of_paper_boxes_and_autotune(tmp_path, monkeypatch):
     assert best["ms_per_step"] > 0
     again = autotune.tune(b, [(w.nx, w.ny) for w in cases], lbm.LBM_F32, b.stream)
     assert again["shape"] == best["shape"] and again["kind"] == best["kind"]  # served from the cache
+    before = [lbm.lbm_force_count(b.case(c)) for c in range(len(cases))]
     b.step(10)
     b.sync()
     for c in range(len(cases)):
+        assert lbm.lbm_force_count(b.case(c)) == before[c] + 10
         cd, cl = b.forces(c)
-        assert len(cd) == 11 and np.all(np.isfinite(cd))
+        assert np.all(np.isfinite(cd))
     b.close()
 
 

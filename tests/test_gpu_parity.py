@@ -34,9 +34,11 @@ def reference_pops(U):
 
 
 @functools.lru_cache(maxsize=64)
-def oracle_run(wl: W.Workload, steps: int):
+def oracle_run(wl: W.Workload, steps: int, mrt: bool = False):
     """Oracle after `steps` steps: f*(steps), forces F(0..steps), fields of f(steps)."""
     o = O.Oracle(wl.nx, wl.ny, wl.tau, wl.U, bc_y=wl.bc, mask=wl.mask())
+    if mrt:
+        o.set_collision(O.MRT, *O.MRT_PAPER_RATES)
     o.init_equilibrium(*wl.initial_fields())
     F = o.run(steps)
     fields = o.fields()
@@ -69,8 +71,8 @@ def offsets_to_f(pops, U, storage=lbm.LBM_F32):
     return g + reference_pops(U)[:, None, None]
 
 
-def compare(wl, steps, pops, F, fields, tol_f, tol_F, storage=lbm.LBM_F32):
-    fs, Fo, (ro, uo, vo) = oracle_run(wl, steps)
+def compare(wl, steps, pops, F, fields, tol_f, tol_F, storage=lbm.LBM_F32, mrt=False):
+    fs, Fo, (ro, uo, vo) = oracle_run(wl, steps, mrt)
     f = offsets_to_f(pops, wl.U, storage)
     fluid = wl.mask() == 0
     df = np.max(np.abs(f - fs)[:, fluid])
@@ -158,6 +160,30 @@ def test_unstable_case_is_flagged_like_the_oracle():
     _, u, v = o.fields()
     with np.errstate(invalid="ignore", over="ignore"):
         assert not np.all(np.sqrt(u * u + v * v) <= 0.3)
+
+
+MRT = dict(collision=lbm.LBM_COLLIDE_MRT, mrt_rates=O.MRT_PAPER_RATES)
+
+
+@pytest.mark.parametrize("kname,kw", KERNELS, ids=[k[0] for k in KERNELS])
+@pytest.mark.parametrize("bc", BCS, ids=[W.BC_NAMES[b] for b in BCS])
+def test_mrt_small_lattices_match_oracle(kname, kw, bc):
+    """The paper's MRT collision (Eq. 6, S = diag[1, 1.1, 1.1, 1, 1.1, 1, 1.1, 1/tau, 1/tau])."""
+    wl = W.random_case(300, 41, seed=500 + bc, bc=bc, D=8, tau=0.56)
+    pops, F, fields, _ = gpu_run(wl, 60, **kw, **MRT)
+    compare(wl, 60, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
+
+
+def test_mrt_parity_small_cylinder_2000_steps():
+    """Re = 100, D = 10, 400 x 200, U = 0.1, tau = 0.53, free-slip, 2000 steps
+    with the paper's MRT collision, which keeps this case stable: max |u - u_ref|
+    <= 1e-5 U and Cd within 1e-4 of the oracle at every step."""
+    wl = W.PARITY_D10
+    pops, F, fields, _ = gpu_run(wl, wl.steps, **MRT)
+    compare(wl, wl.steps, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
+    q = 0.5 * wl.U ** 2 * wl.D
+    _, Fo, _ = oracle_run(wl, wl.steps, True)
+    assert np.max(np.abs(F[:, 0] - Fo[:, 0]) / q) <= 1e-4 * np.max(np.abs(Fo[:, 0]) / q)
 
 
 def test_every_tma_shape_matches_direct():

@@ -1,0 +1,30 @@
+"""Post-processing on synthetic signals with known answers."""
+import math
+
+import numpy as np
+
+from paper_2605_02185_gb300 import postprocess as PP
+
+
+def test_period_of_a_sinusoid():
+    T = 612.7
+    n = np.arange(20000)
+    cl = 0.31 * np.sin(2 * math.pi * n / T + 0.3)
+    assert abs(PP.period_from_crossings(cl) - T) < 0.05
+    assert abs(PP.period_from_spectrum(cl) - T) / T < 2e-3
+    st = PP.statistics(1.4 + 0.01 * np.sin(4 * math.pi * n / T), cl, D=10, U=0.1, periods=10)
+    assert abs(st["st_zc"] - 10 / (0.1 * T)) / (10 / (0.1 * T)) < 1e-3
+    assert abs(st["cl_amp"] - 0.31) < 1e-3 and abs(st["cd_mean"] - 1.4) < 1e-3
+
+
+def test_periodicity_detector():
+    T = 400.0
+    n = np.arange(30000)
+    amp = 0.3 * (1 - np.exp(-n / 3000.0))  # growing, then saturating
+    cl = amp * np.sin(2 * math.pi * n / T)
+    i = PP.periodic_index(cl)
+    assert i is not None
+    # per-period growth 0.3 e^{-n/3000} (1 - e^{-T/3000}) / amp falls below
+    # 0.5 % near n ~ 9.4k; two such periods later the detector fires
+    assert 9000 < i < 12000
+    assert PP.periodic_index(1e-3 * np.sin(2 * math.pi * n / T)) is None  # below the amplitude floor
