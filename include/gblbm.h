@@ -69,6 +69,8 @@ extern "C" {
 #define LBM_KERNEL_AUTO 0   /* the tuned default for the storage type */
 #define LBM_KERNEL_DIRECT 1 /* one thread per cell, loads straight from HBM */
 #define LBM_KERNEL_TMA 2    /* persistent; bulk-async (TMA) row staging */
+#define LBM_KERNEL_TMA_BULK 3 /* TMA row staging and TMA bulk stores of the new rows
+                                 (single lattices; not for batches) */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -184,6 +186,9 @@ int lbm_get_kernel(lbm_ctx *ctx, int *out6);
 /* The shapes the TMA kernel is built for: up to cap triples (compute warps,
  * cells per thread, stages) into out; *count receives how many exist. */
 int lbm_kernel_shapes(int *out, int cap, int *count);
+
+/* The same for LBM_KERNEL_TMA or LBM_KERNEL_TMA_BULK. */
+int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count);
 
 /* The CUDA stream the context launches on (cudaStream_t). */
 int lbm_get_stream(lbm_ctx *ctx, void **stream);

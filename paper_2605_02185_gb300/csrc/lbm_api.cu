@@ -52,6 +52,15 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   return off;
 }
 
+// Index of (ncw, cpt, stages) in the shape list of `kernel`, or -1.
+int find_shape(int kernel, int ncw, int cpt, int stages) {
+  const TmaShape *list = kernel == LBM_KERNEL_TMA_BULK ? kTmaBulkShapes : kTmaShapes;
+  const int n = kernel == LBM_KERNEL_TMA_BULK ? kNumTmaBulkShapes : kNumTmaShapes;
+  for (int s = 0; s < n; ++s)
+    if (list[s].ncw == ncw && list[s].cpt == cpt && list[s].stages == stages) return s;
+  return -1;
+}
+
 // Fill the step parameters for the chosen kernel shape (tile width, force
 // slots) and capture the multi-step graph.
 int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
@@ -59,6 +68,14 @@ int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
   int seg;
   if (kernel == LBM_KERNEL_DIRECT) {
     seg = kDirectThreads;
+  } else if (kernel == LBM_KERNEL_TMA_BULK) {
+    if (shape < 0 || shape >= kNumTmaBulkShapes) return LBM_ERR_ARG;
+    if (c->ops->bulk_smem(shape) > 227 * 1024) return LBM_ERR_ARG;
+    CK(c->ops->bulk_prep(shape));
+    const int occ = c->ops->bulk_occupancy(shape);
+    if (occ <= 0) return LBM_ERR_ARG;
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
+    seg = kTmaBulkShapes[shape].ncw * 32 * kTmaBulkShapes[shape].cpt;
   } else {
     if (shape < 0 || shape >= kNumTmaShapes) return LBM_ERR_ARG;
     if (c->ops->smem(shape) > 227 * 1024) return LBM_ERR_ARG;
@@ -100,6 +117,7 @@ cudaError_t launch_step(lbm_ctx *c, int from) {
   const void *A = c->buf[from];
   void *B = c->buf[from ^ 1];
   if (c->kernel == LBM_KERNEL_DIRECT) return c->ops->direct(A, B, c->p, c->stream);
+  if (c->kernel == LBM_KERNEL_TMA_BULK) return c->ops->tma_bulk(c->shape, c->grid, A, B, c->p, c->stream);
   return c->ops->tma(c->shape, c->grid, A, B, c->p, c->stream);
 }
 
@@ -256,12 +274,9 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   int shape = default_shape(o->storage);
   int kernel = o->kernel;
   int ctas = o->ctas_per_sm > 0 ? o->ctas_per_sm : 1;
+  if (kernel == LBM_KERNEL_TMA_BULK) shape = 0;
   if (o->consumer_warps || o->cells_per_thread || o->stages) {
-    shape = -1;
-    for (int s = 0; s < kNumTmaShapes; ++s)
-      if (kTmaShapes[s].ncw == o->consumer_warps && kTmaShapes[s].cpt == o->cells_per_thread &&
-          kTmaShapes[s].stages == o->stages)
-        shape = s;
+    shape = find_shape(kernel, o->consumer_warps, o->cells_per_thread, o->stages);
     if (shape < 0 && kernel != LBM_KERNEL_DIRECT) return fail(LBM_ERR_ARG);
   } else if (kernel == LBM_KERNEL_AUTO) {
     kernel = default_kernel(o->storage);
@@ -485,15 +500,13 @@ int lbm_set_populations(lbm_ctx *c, const void *src, size_t bytes, int64_t step)
 }
 
 int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int ctas_per_sm) {
-  if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA) return LBM_ERR_ARG;
+  if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
-  int shape = default_shape(c->o.storage);
+  int shape = kernel == LBM_KERNEL_TMA_BULK ? 0 : default_shape(c->o.storage);
   int ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
   if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
-    shape = -1;
-    for (int s = 0; s < kNumTmaShapes; ++s)
-      if (kTmaShapes[s].ncw == ncw && kTmaShapes[s].cpt == cpt && kTmaShapes[s].stages == stages) shape = s;
+    shape = find_shape(kernel, ncw, cpt, stages);
     if (shape < 0) return LBM_ERR_ARG;
   } else if (kernel == LBM_KERNEL_AUTO) {
     kernel = default_kernel(c->o.storage);
@@ -507,10 +520,11 @@ int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int cta
 int lbm_get_kernel(lbm_ctx *c, int *out6) {
   if (!c || !out6) return LBM_ERR_ARG;
   const bool tma = c->kernel != LBM_KERNEL_DIRECT;
+  const TmaShape &sh = c->kernel == LBM_KERNEL_TMA_BULK ? kTmaBulkShapes[c->shape] : kTmaShapes[c->shape];
   out6[0] = c->kernel;
-  out6[1] = tma ? kTmaShapes[c->shape].ncw : kDirectThreads / 32;
-  out6[2] = tma ? kTmaShapes[c->shape].cpt : 1;
-  out6[3] = tma ? kTmaShapes[c->shape].stages : 0;
+  out6[1] = tma ? sh.ncw : kDirectThreads / 32;
+  out6[2] = tma ? sh.cpt : 1;
+  out6[3] = tma ? sh.stages : 0;
   out6[4] = tma ? c->ctas_per_sm : 0;
   out6[5] = c->grid;
   return LBM_OK;
@@ -523,6 +537,20 @@ int lbm_kernel_shapes(int *out, int cap, int *count) {
     out[3 * s] = kTmaShapes[s].ncw;
     out[3 * s + 1] = kTmaShapes[s].cpt;
     out[3 * s + 2] = kTmaShapes[s].stages;
+  }
+  return LBM_OK;
+}
+
+int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count) {
+  if (kernel != LBM_KERNEL_TMA && kernel != LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (!count || cap < 0 || (cap > 0 && !out)) return LBM_ERR_ARG;
+  const TmaShape *list = kernel == LBM_KERNEL_TMA_BULK ? kTmaBulkShapes : kTmaShapes;
+  const int n = kernel == LBM_KERNEL_TMA_BULK ? kNumTmaBulkShapes : kNumTmaShapes;
+  *count = n;
+  for (int s = 0; s < n && s < cap; ++s) {
+    out[3 * s] = list[s].ncw;
+    out[3 * s + 1] = list[s].cpt;
+    out[3 * s + 2] = list[s].stages;
   }
   return LBM_OK;
 }

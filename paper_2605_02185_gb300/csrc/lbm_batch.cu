@@ -79,6 +79,7 @@ int batch_sizes(int n, const lbm_case *cases, const lbm_opts *common, std::vecto
 // Give every case the tile width of the batch kernel, then upload the
 // per-case descriptors with the batch-wide tile offsets.
 int configure_batch(lbm_batch *b, int kernel, int shape, int ctas) {
+  if (kernel == LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;  // single-lattice kernel only
   const TmaShape &ts = kTmaShapes[shape];
   for (lbm_ctx *c : b->cases) {
     const int rc = kernel == LBM_KERNEL_DIRECT ? lbm_set_kernel(c, LBM_KERNEL_DIRECT, 0, 0, 0, 1)

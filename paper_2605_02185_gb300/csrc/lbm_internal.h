@@ -33,6 +33,11 @@ struct KernelOps {
   // initial state from device float fields, optionally with non-equilibrium part
   cudaError_t (*init_device)(void *A, const StepParams &p, const float *rho, const float *u, const float *v,
                              int with_noneq, double tau, cudaStream_t st);
+  // the TMA-load + TMA-bulk-store step kernel, shapes of GBLBM_TMA_BULK_SHAPES
+  cudaError_t (*tma_bulk)(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st);
+  cudaError_t (*bulk_prep)(int shape);
+  int (*bulk_occupancy)(int shape);
+  size_t (*bulk_smem)(int shape);
 };
 
 const KernelOps *ops_f32();
@@ -58,6 +63,14 @@ const KernelOps *ops_f64();
   X(13, 16, 2, 2)           \
   X(14, 4, 2, 3)
 
+// Shapes of the TMA-load + TMA-bulk-store kernel X(id, warps, cells/thread, stages).
+#define GBLBM_TMA_BULK_SHAPES(X) \
+  X(0, 12, 2, 4)                 \
+  X(1, 12, 2, 3)                 \
+  X(2, 8, 2, 4)                  \
+  X(3, 16, 1, 4)                 \
+  X(4, 8, 4, 3)
+
 struct TmaShape {
   int ncw, cpt, stages;
 };
@@ -65,5 +78,9 @@ struct TmaShape {
 constexpr TmaShape kTmaShapes[] = {GBLBM_TMA_SHAPES(GBLBM_SHAPE_ENTRY)};
 #undef GBLBM_SHAPE_ENTRY
 constexpr int kNumTmaShapes = (int)(sizeof(kTmaShapes) / sizeof(kTmaShapes[0]));
+#define GBLBM_SHAPE_ENTRY(id, a, b, c) {a, b, c},
+constexpr TmaShape kTmaBulkShapes[] = {GBLBM_TMA_BULK_SHAPES(GBLBM_SHAPE_ENTRY)};
+#undef GBLBM_SHAPE_ENTRY
+constexpr int kNumTmaBulkShapes = (int)(sizeof(kTmaBulkShapes) / sizeof(kTmaBulkShapes[0]));
 
 }  // namespace gblbm

@@ -45,15 +45,14 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
 }
 
 // One node, general form: pull (with bounce-back and placeholders), boundary
-// rules, collision; stores h*(x) into B and adds the node's links to the force.
+// rules, collision into h; adds the node's links to the force.
 template <int MRT, class S, class Fetch>
-__device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
-                                            int y, typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
-                                            double &fx, double &fy, bool &bad) {
+__device__ __forceinline__ void node_compute(const S *__restrict__ A, const StepParams &p, int x, int y,
+                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
+                                             double &fx, double &fy, bool &bad, typename Store<S>::C (&h)[9]) {
   using C = typename Store<S>::C;
   const int xe = (x == p.nx - 1) ? p.nx - 2 : x;  // Eq. 13: outlet = column nx-2
   const uint32_t lm = link_mask(p, xe, y);
-  C h[9];
   if (lm & LM_SOLID) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) h[k] = (C)0;
@@ -64,26 +63,45 @@ __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restri
     bad |= !(uu <= (C)0.09);
     if ((lm & LM_LINKS) && x == xe) link_force<C>(h, lm, fx, fy);
   }
-  S *o = B + (size_t)y * p.pitch + x;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
 }
 
 // One interior fluid node away from every boundary and link (plain_span):
 // every source is regular, no rule applies.
 template <int MRT, class S, class Fetch>
-__device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams &p, int x, int y,
-                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
-                                             bool &bad) {
+__device__ __forceinline__ void plain_compute(const StepParams &p, int x, int y, typename Store<S>::C omega,
+                                              typename Store<S>::C U, Fetch fetch, bool &bad,
+                                              typename Store<S>::C (&h)[9]) {
   using C = typename Store<S>::C;
-  C h[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = fetch(k, x - CX(k), y - CY(k));
   const C uu = collide_model<MRT, C>(h, p, omega, U);
   bad |= !(uu <= (C)0.09);
+}
+
+template <class S>
+__device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &p, int x, int y,
+                                           const typename Store<S>::C (&h)[9]) {
   S *o = B + (size_t)y * p.pitch + x;
 #pragma unroll
   for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
+}
+
+template <int MRT, class S, class Fetch>
+__device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
+                                            int y, typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
+                                            double &fx, double &fy, bool &bad) {
+  typename Store<S>::C h[9];
+  node_compute<MRT, S>(A, p, x, y, omega, U, fetch, fx, fy, bad, h);
+  store_node<S>(B, p, x, y, h);
+}
+
+template <int MRT, class S, class Fetch>
+__device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams &p, int x, int y,
+                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
+                                             bool &bad) {
+  typename Store<S>::C h[9];
+  plain_compute<MRT, S>(p, x, y, omega, U, fetch, bad, h);
+  store_node<S>(B, p, x, y, h);
 }
 
 // ---- direct kernel: one CTA per row tile, loads straight from HBM -------
@@ -417,6 +435,167 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
   }
 }
 
+// ---- TMA loads + TMA bulk stores ----------------------------------------
+// The single-lattice pipeline of step_tma, but the compute warps write the
+// new f* of a row tile into a shared-memory output tile (two, alternating)
+// and one thread stores each of its nine plane rows with a bulk async copy
+// (cp.async.bulk global <- shared).  A node then costs nine shared-memory
+// stores instead of nine global stores with their 64-bit address arithmetic,
+// which matters where the step is issue-bound (16-bit storage, MRT).
+template <class S, int NCW, int CPT, int STAGES>
+constexpr size_t tma_bulk_smem_bytes() {
+  return ((size_t)STAGES * 9 * (NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t) +
+          15) / 16 * 16 +
+         (size_t)2 * 9 * NCW * 32 * CPT * sizeof(S);
+}
+
+__device__ __forceinline__ void bulk_s2g(void *dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <class S, int NCW, int CPT, int STAGES, int MRT>
+__global__ void __launch_bounds__((NCW + 1) * 32)
+    step_tma_bulk(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
+  using C = typename Store<S>::C;
+  constexpr int H = 16 / (int)sizeof(S);
+  constexpr int NC = NCW * 32;
+  constexpr int W = NC * CPT;
+  constexpr int SEG = W + 2 * H;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S *tiles = reinterpret_cast<S *>(smem);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
+  S *outs = reinterpret_cast<S *>(
+      smem + (((size_t)STAGES * 9 * SEG * sizeof(S) + 2 * STAGES * sizeof(uint64_t) + 15) / 16 * 16));
+  __shared__ double red[2][NCW];
+  __shared__ int s_last;
+  __shared__ int s_abort_store;
+  volatile int *s_abort = &s_abort_store;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = p.ny * p.nseg;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(smem_addr(&bars[q]), 1);
+      mbar_init(smem_addr(&bars[STAGES + q]), NCW);
+    }
+    *s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NCW) {  // ---------------- producer (as in step_tma)
+    if (lane == 0) {
+      int j = 0;
+      for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+        const int st = j % STAGES;
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+          if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
+          *s_abort = 1;
+          break;
+        }
+        if (*s_abort) break;
+        const int y = t / p.nseg, s = t - y * p.nseg;
+        const int x0 = s * W;
+        const int xs = max(x0 - H, 0), xl = min(x0 + W + H, p.pitch);
+        const uint32_t bytes = (uint32_t)(xl - xs) * (uint32_t)sizeof(S);
+        int rows[9];
+        uint32_t total = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          int sy = y - CY(k);
+          if (p.bc == BC_PERIODIC) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+          rows[k] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
+          total += rows[k] >= 0 ? bytes : 0u;
+        }
+        const uint32_t fb = smem_addr(&bars[st]);
+        mbar_arrive_expect_tx(fb, total);
+        S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (rows[k] >= 0)
+            bulk_g2s(smem_addr(dst + (size_t)k * SEG), A + (size_t)k * p.plane + (size_t)rows[k] * p.pitch + xs, bytes,
+                     fb);
+      }
+      for (int q = max(0, j - STAGES); q < j; ++q) {
+        const uint32_t fb = smem_addr(&bars[q % STAGES]);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
+          if (global_ns() - t0 > 1000000000ull) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------------- compute warps
+  const int ctid = threadIdx.x;
+  const C omega = (C)p.omega, U = (C)p.U;
+  bool bad = false;
+  int j = 0;
+  for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
+    const int st = j % STAGES;
+    bool ok = false;
+    if (!*s_abort) {
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      if (!ok && !*s_abort) {
+        atomicOr(p.err, ERR_TIMEOUT);
+        *s_abort = 1;
+      }
+    }
+    const int y = t / p.nseg, s = t - y * p.nseg;
+    const int x0 = s * W;
+    double fx = 0.0, fy = 0.0;
+    S *out = outs + (size_t)(j & 1) * 9 * W;
+    if (ok) {
+      const S *tile = tiles + (size_t)st * 9 * SEG + (H - x0);
+      auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int xw = x0 + c * NC + (ctid & ~31);
+        const int x = xw + lane;
+        C h[9];
+        if (plain_span(p, xw, xw + 31, y)) {
+          plain_compute<MRT, S>(p, x, y, omega, U, fetch, bad, h);
+        } else if (x < p.nx) {
+          node_compute<MRT, S>(A, p, x, y, omega, U, fetch, fx, fy, bad, h);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) h[k] = (C)0;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out[k * W + (x - x0)] = Store<S>::st(h[k]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
+    }
+    fence_proxy_async_smem();
+    // the bulk store that last read the other output tile has finished
+    if (ctid == 0) bulk_wait_read0();
+    named_bar(2, NC);
+    if (ok && ctid == 0) {
+      const int xl = min(x0 + W, p.pitch);
+      const uint32_t bytes = (uint32_t)(xl - x0) * (uint32_t)sizeof(S);
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        bulk_s2g(B + (size_t)k * p.plane + (size_t)y * p.pitch + x0, smem_addr(out + k * W), bytes);
+      bulk_commit();
+    }
+    if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
+  }
+  if (ctid == 0) bulk_wait0();
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+}
+
 template <class S, int NCW, int CPT, int STAGES>
 constexpr size_t tma_smem_bytes() {
   return (size_t)STAGES * 9 * (NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t);
@@ -680,6 +859,79 @@ struct Launch {
     return 0;
   }
 
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t bulk_one(int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
+    constexpr size_t smem = tma_bulk_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (p.mrt)
+      step_tma_bulk<S, NCW, CPT, STAGES, 1><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    else
+      step_tma_bulk<S, NCW, CPT, STAGES, 0><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    return cudaGetLastError();
+  }
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t bulk_prep_one() {
+    constexpr size_t smem = tma_bulk_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const cudaError_t e = cudaFuncSetAttribute(step_tma_bulk<S, NCW, CPT, STAGES, 0>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_tma_bulk<S, NCW, CPT, STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  }
+  template <int NCW, int CPT, int STAGES>
+  static int bulk_occ_one() {
+    constexpr size_t smem = tma_bulk_smem_bytes<S, NCW, CPT, STAGES>();
+    if (smem > 227 * 1024) return 0;
+    int n = 0, m = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_tma_bulk<S, NCW, CPT, STAGES, 0>, (NCW + 1) * 32,
+                                                      smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, step_tma_bulk<S, NCW, CPT, STAGES, 1>, (NCW + 1) * 32,
+                                                      smem) != cudaSuccess)
+      return 0;
+    return n < m ? n : m;
+  }
+  static cudaError_t tma_bulk(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return bulk_one<a, b, c>(grid, A, B, p, st);
+      GBLBM_TMA_BULK_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t bulk_prep(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return bulk_prep_one<a, b, c>();
+      GBLBM_TMA_BULK_SHAPES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+  }
+  static int bulk_occupancy(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return bulk_occ_one<a, b, c>();
+      GBLBM_TMA_BULK_SHAPES(X)
+#undef X
+    }
+    return 0;
+  }
+  static size_t bulk_smem(int shape) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return tma_bulk_smem_bytes<S, a, b, c>();
+      GBLBM_TMA_BULK_SHAPES(X)
+#undef X
+    }
+    return 0;
+  }
+
   static cudaError_t init(void *A, const StepParams &p, const double *r, const double *u, const double *v, int y0,
                           int rows, cudaStream_t st) {
     const long long n = (long long)rows * p.nx;
@@ -769,7 +1021,8 @@ struct Launch {
   static const KernelOps *table() {
     static const KernelOps ops = {(int)sizeof(S), &direct,     &tma,          &prep,     &occupancy,
                                   &smem,          &init,       &force,        &fields,   &mass_rows,
-                                  &batch_direct,  &batch_tma,  &batch_prep, &init_device};
+                                  &batch_direct,  &batch_tma,  &batch_prep, &init_device,
+                                  &tma_bulk,      &bulk_prep,  &bulk_occupancy, &bulk_smem};
     return &ops;
   }
 };

@@ -24,7 +24,7 @@ LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT = -1, -2, -3, -4
 LBM_ERR_OOM, LBM_ERR_RANGE, LBM_ERR_STATE = -5, -6, -7
 LBM_BC_FREESLIP, LBM_BC_PERIODIC, LBM_BC_ZOUHE = 0, 1, 2
 LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64 = 0, 1, 2, 3
-LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK = 0, 1, 2, 3
 LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
 ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8}
 ELEM_NUMPY = {LBM_F32: np.float32, LBM_F16_OFS: np.float16, LBM_BF16_OFS: np.uint16, LBM_F64: np.float64}
@@ -99,6 +99,7 @@ def load_library(path: str | None = None):
         "lbm_set_kernel": (i, [vp, i, i, i, i, i]),
         "lbm_get_kernel": (i, [vp, vp]),
         "lbm_kernel_shapes": (i, [vp, i, ctypes.POINTER(i)]),
+        "lbm_kernel_shapes_for": (i, [i, vp, i, ctypes.POINTER(i)]),
         "lbm_get_stream": (i, [vp, ctypes.POINTER(vp)]),
         "lbm_launch_count": (i, [vp, ctypes.POINTER(i64)]),
         "lbm_bytes_per_step": (i, [vp, ctypes.POINTER(d)]),
@@ -301,11 +302,12 @@ def lbm_get_kernel(h) -> dict:
     return dict(zip(keys, (int(v) for v in out)))
 
 
-def lbm_kernel_shapes() -> list:
+def lbm_kernel_shapes(kernel: int = LBM_KERNEL_TMA) -> list:
     n = ctypes.c_int()
-    _check(load_library().lbm_kernel_shapes(None, 0, ctypes.byref(n)), "lbm_kernel_shapes")
+    _check(load_library().lbm_kernel_shapes_for(int(kernel), None, 0, ctypes.byref(n)), "lbm_kernel_shapes_for")
     out = np.zeros(3 * n.value, np.int32)
-    _check(load_library().lbm_kernel_shapes(_p(out), n.value, ctypes.byref(n)), "lbm_kernel_shapes")
+    _check(load_library().lbm_kernel_shapes_for(int(kernel), _p(out), n.value, ctypes.byref(n)),
+           "lbm_kernel_shapes_for")
     return [tuple(int(v) for v in out[3 * i:3 * i + 3]) for i in range(n.value)]
 
 

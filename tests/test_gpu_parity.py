@@ -363,3 +363,28 @@ def test_full_size_lattice_sampled_windows():
         if name == "cylinder":
             assert np.max(np.abs(F - Fo)) <= 1e-6 * np.max(np.abs(Fo)), (F, Fo)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_F32, lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS])
+def test_bulk_store_kernel_matches_direct(storage):
+    """TMA loads + TMA bulk stores: the same per-node arithmetic, identical bits."""
+    shapes = lbm.lbm_kernel_shapes(lbm.LBM_KERNEL_TMA_BULK)
+    assert len(shapes) >= 3
+    for wl in (W.random_case(613, 57, seed=21, bc=W.BC_FREESLIP, D=10),
+               W.random_case(769, 33, seed=8, bc=W.BC_ZOUHE, D=8),   # outlet alone at a 768-node tile start
+               W.random_case(1025, 29, seed=9, bc=W.BC_PERIODIC, D=8)):
+        ref, Fr, _, _ = gpu_run(wl, 25, kernel=lbm.LBM_KERNEL_DIRECT, storage=storage)
+        for shape in shapes:
+            for ctas in (1, 2):
+                for coll in (lbm.LBM_COLLIDE_BGK,):
+                    pops, F, _, info = gpu_run(wl, 25, kernel=lbm.LBM_KERNEL_TMA_BULK, shape=shape,
+                                               ctas_per_sm=ctas, storage=storage, collision=coll)
+                    assert info["kernel"] == lbm.LBM_KERNEL_TMA_BULK
+                    assert np.array_equal(pops.view(np.uint8), ref.view(np.uint8)), (wl.name, shape, ctas)
+                    assert np.array_equal(F, Fr), (wl.name, shape, ctas)
+
+
+def test_bulk_store_kernel_mrt_matches_oracle():
+    wl = W.random_case(300, 41, seed=501, bc=W.BC_ZOUHE, D=8, tau=0.56)
+    pops, F, fields, _ = gpu_run(wl, 60, kernel=lbm.LBM_KERNEL_TMA_BULK, **MRT)
+    compare(wl, 60, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)

@@ -14,7 +14,7 @@ from paper_2605_02185_gb300 import warmstart as WS  # noqa: E402
 
 
 def test_warm_start_gains_over_cold_start():
-    cfg = WS.Config(D=20, train_cases=8, snapshots=1200, batch=4, lr=2e-3, lr_final=2e-4, stride=23,
+    cfg = WS.Config(D=20, train_cases=8, snapshots=2000, batch=4, lr=3e-4, lr_final=3e-5, stride=23,
                     spinup_max=300_000, eval_max=300_000, chunk=500)
     dev = torch.device("cuda")
     net, info = WS.train(cfg, dev, log=lambda m: None)
