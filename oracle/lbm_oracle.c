@@ -26,6 +26,12 @@
  *     top f5=f3, f8=f7, f9=f6; bottom f3=f5, f7=f8, f6=f9 (paper 1-based i).
  *   - Zou-He top/bottom (Eqs. 9-10) take u = U (the inlet speed) and the
  *     wall-normal Zou-He density rho_w.
+ *   - Constant-velocity bounce-back top/bottom (Eq. 11) moves both walls at
+ *     (U, 0) (Section 2.3.4: the inlet velocity), reflects the node's own
+ *     post-collision populations within the step, and takes rho as the
+ *     density of that post-collision state.  Eq. 11b repeats "top" and the
+ *     top's indices; it is read as the bottom rule with the bottom's
+ *     indices (f3, f6, f7 from f*5, f*8, f*9).
  *   - The inlet (Section 3.1, "non-equilibrium bounce-back at the inlet") is
  *     the Zou-He west velocity boundary with velocity (U, 0).
  *   - The outlet (Eq. 13) copies all nine populations from column nx-2 into
@@ -61,7 +67,7 @@ static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
-enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_WALLS = 3 };
+enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_WALLS = 3, ORC_Y_MOVING = 4 };
 enum { ORC_X_INOUT = 0, ORC_X_PERIODIC = 1 };
 
 /* Eq. 6: the MRT transformation matrix M as printed (rows: rho, e, epsilon,
@@ -79,6 +85,7 @@ typedef struct {
   int model;            /* ORC_BGK or ORC_MRT */
   double s[9];          /* MRT relaxation rates, diagonal of S */
   double tau, U;
+  double uw_top, uw_bot; /* wall speeds of the constant-velocity bounce-back (default U) */
   double gx, gy;       /* test-only body force density (Guo forcing) */
   unsigned char *solid; /* [ny][nx], 1 = solid node */
   double *f;            /* populations after stream + boundaries, f(n) */
@@ -210,6 +217,8 @@ orc_t *orc_create(int nx, int ny, double tau, double U, int bc_y, int bc_x, cons
   o->ny = ny;
   o->tau = tau;
   o->U = U;
+  o->uw_top = U;
+  o->uw_bot = U;
   o->bc_y = bc_y;
   o->bc_x = bc_x;
   o->model = ORC_BGK;
@@ -399,6 +408,28 @@ static void zouhe_inlet(double *f, double U) {
   f[8] = f[6] + 0.5 * (f[2] - f[4]) + (1.0 / 6.0) * rho * U; /* f9 */
 }
 
+/* Section 2.3.4, Eq. 11: constant-velocity (moving-wall) bounce-back.  Each
+ * population that leaves the node (x, y) through the wall, f*_i(x) with c_i
+ * pointing into the wall, returns in the same step as f_opp(i)(x) less
+ * 2 w_i rho (c_i . u_w) / c_s^2, c_s^2 = 1/3, u_w = (uw, 0), rho the density
+ * of the node's f*(x).  Top (into = +1): i = 3, 6, 7 -> 5, 8, 9 (Eq. 11a);
+ * bottom (into = -1): i = 5, 8, 9 -> 3, 6, 7 (Eq. 11b, read with the bottom's
+ * indices). */
+static void moving_wall(const orc_t *o, int x, int y, int into, double uw, double *f) {
+  double fs[9], rho = 0.0;
+  for (int k = 0; k < 9; ++k) {
+    fs[k] = o->fs[IDX(o, k, x, y)];
+    rho += fs[k];
+  }
+  for (int k = 1; k < 9; ++k)
+    if (CY[k] == into) f[opposite(k)] = fs[k] - 2.0 * WT[k] * rho * (CX[k] * uw) * 3.0;
+}
+
+void orc_set_wall_velocity(orc_t *o, double uw_top, double uw_bot) {
+  o->uw_top = uw_top;
+  o->uw_bot = uw_bot;
+}
+
 static void load9(const orc_t *o, int x, int y, double *f) {
   for (int k = 0; k < 9; ++k) f[k] = o->f[IDX(o, k, x, y)];
 }
@@ -431,6 +462,20 @@ void orc_boundaries(orc_t *o) {
       else
         zouhe_bottom(f, o->U);
       store9(o, x, y, f);
+    }
+  }
+  if (o->bc_y == ORC_Y_MOVING) {
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[(size_t)(ny - 1) * nx + x]) continue;
+      load9(o, x, ny - 1, f);
+      moving_wall(o, x, ny - 1, +1, o->uw_top, f);
+      store9(o, x, ny - 1, f);
+    }
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[x]) continue;
+      load9(o, x, 0, f);
+      moving_wall(o, x, 0, -1, o->uw_bot, f);
+      store9(o, x, 0, f);
     }
   }
   if (o->bc_x == ORC_X_INOUT) {

@@ -24,7 +24,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(BUILD_DIR, "liblbm_oracle.so")
 
-Y_FREESLIP, Y_PERIODIC, Y_ZOUHE, Y_WALLS = 0, 1, 2, 3
+Y_FREESLIP, Y_PERIODIC, Y_ZOUHE, Y_WALLS, Y_MOVING = 0, 1, 2, 3, 4
 X_INOUT, X_PERIODIC = 0, 1
 
 _lib = None
@@ -49,6 +49,7 @@ def _bind(lib):
     lib.orc_create.argtypes = [i, i, d, d, i, i, p]
     lib.orc_destroy.argtypes = [p]
     lib.orc_set_body_force.argtypes = [p, d, d]
+    lib.orc_set_wall_velocity.argtypes = [p, d, d]
     lib.orc_init_equilibrium.argtypes = [p, p, p, p]
     for name in ("orc_set_f", "orc_get_f", "orc_set_fs", "orc_get_fs"):
         getattr(lib, name).argtypes = [p, p]
@@ -181,6 +182,10 @@ class Oracle:
 
     def set_collision(self, model, s_e=1.1, s_eps=1.1, s_q=1.1):
         self.lib.orc_set_collision(self.h, int(model), float(s_e), float(s_eps), float(s_q))
+
+    def set_wall_velocity(self, uw_top, uw_bot):
+        """Wall speeds of the constant-velocity bounce-back (Y_MOVING); both U by default."""
+        self.lib.orc_set_wall_velocity(self.h, float(uw_top), float(uw_bot))
 
     def set_body_force(self, gx, gy):
         self.lib.orc_set_body_force(self.h, float(gx), float(gy))

@@ -79,6 +79,13 @@ def equilibrium_second_moment_ok(lib):
             and abs((f * cx * cy).sum() - rho * ux * uy) <= 4e-16)
 
 
+def couette_exact(lib, rho0=1.0):
+    ny, ut, ub = 16, 0.05, -0.02
+    _, u, _ = P.couette(ny, ut, ub, rho0, steps=12_000, lib=lib)
+    y = np.arange(ny)[:, None]
+    return np.max(np.abs(u - (ub + (ut - ub) * (y + 0.5) / ny))) <= 1e-10
+
+
 def single_population_moves_by_c(lib):
     cx, cy, _, _ = O.constants(lib)
     nx, ny = 5, 4
@@ -112,6 +119,12 @@ MUTANTS = [
      outlet_copies),
     ("stream_wrong_sign", "neighbour(o, x, y, k, -1, &sx, &sy)", "neighbour(o, x, y, k, +1, &sx, &sy)",
      single_population_moves_by_c),
+    ("moving_wall_factor", "fs[k] - 2.0 * WT[k] * rho", "fs[k] - 1.0 * WT[k] * rho", couette_exact),
+    ("moving_wall_sign", "fs[k] - 2.0 * WT[k] * rho", "fs[k] + 2.0 * WT[k] * rho", couette_exact),
+    ("moving_wall_unit_density", "WT[k] * rho * (CX[k] * uw)", "WT[k] * 1.0 * (CX[k] * uw)",
+     lambda lib: couette_exact(lib, rho0=1.5)),
+    ("moving_wall_not_reversed", "if (CY[k] == into) f[opposite(k)] = fs[k]", "if (CY[k] == into) f[k] = fs[k]",
+     couette_exact),
 ]
 
 
