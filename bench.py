@@ -39,10 +39,10 @@ METRIC = "GLUPS + % HBM roofline (D2Q9 BGK cylinder); wall time to periodic Cd/C
 UNIT = "GLUPS"
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel
-# from one ncu capture, with the kernel-source digest it was taken for; the
-# figure is reported only while the step kernel source is unchanged.
-NCU_TRAFFIC = {"digest": "8630e5c9abb5c9d5", "bytes_per_node": (4679263744 + 4562203392) / 128e6,
-               "capture": "profiles/step_tma_f32_throughput_dram.md"}
+# on the 16000 x 8000 lattice, per storage form, from one ncu capture each,
+# with the kernel-source digest they were taken for; a figure is reported
+# only while the step kernel source is unchanged.
+NCU_TRAFFIC = {"digest": "", "bytes_per_node": {}, "capture": "profiles/step_tma_throughput_dram.md"}
 
 
 # ----------------------------------------------------------------- helpers
@@ -281,8 +281,8 @@ def run_ours(args, workload):
     achieved = bytes_step / per_launch_s / 1e9
     digest = kernel_digest()
     traffic = None
-    if NCU_TRAFFIC["digest"] == digest and NCU_TRAFFIC["bytes_per_node"] and storage == lbm.LBM_F32:
-        traffic = NCU_TRAFFIC["bytes_per_node"] * nx * ny
+    if NCU_TRAFFIC["digest"] == digest and args.storage in NCU_TRAFFIC["bytes_per_node"]:
+        traffic = NCU_TRAFFIC["bytes_per_node"][args.storage] * nx * ny
     info = lat.kernel_info()
 
     # ---- end to end through the C ABI with host buffers
@@ -449,6 +449,75 @@ def run_warmstart(args):
     return 0
 
 
+def run_statistics(args):
+    """Physics of the production case (Re = 100, D = 80, 3200 x 1600, U = 0.05,
+    tau = 0.62, or the case --D/--U/--Re give): each (top/bottom rule,
+    storage form) runs --stat-steps steps from the seeded perturbed start;
+    mean Cd, Cl amplitude and Strouhal number over the last --window steps
+    (Eq. 15, the lift spectrum), the step at which the lift turned periodic,
+    and the relative errors of every storage form against the FP64 run of the
+    same rule."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2605_02185_gb300 import lbm, postprocess
+    from paper_2605_02185_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    base = W.PRODUCTION_D80
+    if args.D or args.U or args.Re:
+        D, U, Re = args.D or base.D, args.U or base.U, args.Re or base.Re
+        base = W.cylinder_case(D, U, Re, seed=base.seed, perturb=base.perturb, name=f"cyl_Re{Re:g}_D{D}_U{U:g}")
+    bc_ids = {"freeslip": W.BC_FREESLIP, "periodic": W.BC_PERIODIC, "zouhe": W.BC_ZOUHE,
+              "movingwall": W.BC_MOVINGWALL}
+    st_ids = {"f32": lbm.LBM_F32, "f16": lbm.LBM_F16_OFS, "bf16": lbm.LBM_BF16_OFS, "f64": lbm.LBM_F64}
+    coll = lbm.LBM_COLLIDE_MRT if args.collision == "mrt" else lbm.LBM_COLLIDE_BGK
+    runs = []
+    for item in args.runs.split(","):
+        bc, st = item.split(":")
+        runs.append((bc, st))
+    stream = torch.cuda.Stream(device)
+    rows, total_nodes, total_s = [], 0, 0.0
+    for bc, st in runs:
+        wl = dataclasses.replace(base, bc=bc_ids[bc])
+        lat = lbm.lattice_for(wl, storage=st_ids[st], stream=stream, device=device, collision=coll,
+                              history_capacity=args.stat_steps + 16)
+        lat.init_fields(*wl.initial_fields())
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        lat.step(args.stat_steps)
+        lat.sync()
+        dt = time.perf_counter() - t0
+        cd, cl = lat.forces(0, args.stat_steps)
+        lat.close()
+        i0 = len(cl) - args.window
+        stats = postprocess.statistics(cd[i0:], cl[i0:], wl.D, wl.U)
+        per = postprocess.periodic_index(cl)
+        row = {"bc": bc, "storage": st, "cd_mean": stats["cd_mean"], "cl_amp": stats["cl_amp"], "st": stats["st"],
+               "st_zero_crossings": stats["st_zc"], "periodic_at_step": per, "seconds": dt,
+               "glups": wl.nx * wl.ny * args.stat_steps / dt / 1e9}
+        rows.append(row)
+        total_nodes += wl.nx * wl.ny * args.stat_steps
+        total_s += dt
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    errors = {}
+    for r in rows:
+        ref = next((q for q in rows if q["bc"] == r["bc"] and q["storage"] == "f64"), None)
+        if ref is not None and r is not ref:
+            errors[f"{r['bc']}:{r['storage']}"] = {k: abs(r[k] - ref[k]) / abs(ref[k]) for k in ("cd_mean", "cl_amp", "st")}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "mean Cd, Cl amplitude, Strouhal number (Eq. 15, lift spectrum)", "unit": "GLUPS",
+            "value": total_nodes / total_s / 1e9, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "dtype": ",".join(sorted({st for _, st in runs})), "steps": args.stat_steps,
+            "config": {"workload": base.name, "nx": base.nx, "ny": base.ny, "D": base.D, "U": base.U,
+                       "tau": base.tau, "Re": base.Re, "collision": args.collision, "window": args.window},
+            "runs": rows, "errors_vs_f64": errors}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,7 +531,15 @@ def main(argv=None):
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="0: the library's tuned default")
     ap.add_argument("--workload", default="throughput",
-                    choices=["throughput", "production", "parity", "batch", "warmstart"])
+                    choices=["throughput", "production", "parity", "batch", "warmstart", "statistics"])
+    ap.add_argument("--runs", default="freeslip:f64,freeslip:f32,freeslip:f16,freeslip:bf16,periodic:f32,"
+                                      "zouhe:f32,movingwall:f32",
+                    help="statistics workload: comma list of top/bottom rule:storage")
+    ap.add_argument("--stat-steps", type=int, default=300_000, help="statistics workload: steps per run")
+    ap.add_argument("--window", type=int, default=100_000, help="statistics workload: averaging window (steps)")
+    ap.add_argument("--D", type=int, default=0, help="statistics workload: cylinder diameter (default 80)")
+    ap.add_argument("--U", type=float, default=0.0, help="statistics workload: inlet speed (default 0.05)")
+    ap.add_argument("--Re", type=float, default=0.0, help="statistics workload: Reynolds number (default 100)")
     ap.add_argument("--snapshots", type=int, default=20000, help="warmstart workload: training snapshots")
     ap.add_argument("--eval-cases", type=int, default=16, help="warmstart workload: held-out Re values")
     ap.add_argument("--cases", type=int, default=64, help="batch workload: number of cases")
@@ -478,6 +555,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "statistics":
+        return run_statistics(args)
     wl = {"throughput": W.THROUGHPUT_D400, "production": W.PRODUCTION_D80, "parity": W.PARITY_D10}[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -52,6 +52,7 @@ extern "C" {
 #define LBM_BC_FREESLIP 0 /* Eq. 7: specular same-node copy */
 #define LBM_BC_PERIODIC 1 /* Eq. 8: wrap in y */
 #define LBM_BC_ZOUHE 2    /* Eqs. 9-10: Zou-He velocity (U, 0) */
+#define LBM_BC_MOVINGWALL 3 /* Eq. 11: constant-velocity bounce-back, walls at (U, 0) */
 
 /* ---- population storage ------------------------------------------------
  * Populations are stored as offsets h_i = f_i - r_i from the free-stream
@@ -123,10 +124,13 @@ void lbm_destroy(lbm_ctx *ctx);
 int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u, const double *v);
 
 /* The same from DEVICE float arrays [ny][nx] (e.g. a network's prediction).
- * with_noneq != 0 adds the first-order Chapman-Enskog non-equilibrium part
- * f_neq_i = -(tau w_i rho / c_s^2) Q_i : grad u, Q_i = c_i c_i - c_s^2 I, with
- * central differences (one-sided next to the lattice edge or the body), so
- * the start carries the stresses of the given velocity field. */
+ * with_noneq != 0 makes f(0) = f_eq + f_neq with the first-order
+ * Chapman-Enskog non-equilibrium part f_neq_i = -(tau w_i rho / c_s^2)
+ * Q_i : grad u, Q_i = c_i c_i - c_s^2 I, central differences (one-sided next
+ * to the lattice edge or the body), so the start carries the stresses of the
+ * given velocity field; the device then holds its collision
+ * f*(0) = f_eq + (1 - 1/tau) f_neq (the shear moments relax at 1/tau in BGK
+ * and in the MRT of Eq. 6 alike). */
 int lbm_init_fields_device(lbm_ctx *ctx, const float *rho, const float *u, const float *v, int with_noneq);
 
 /* Advance n >= 0 steps (asynchronous on the context stream).  Step n maps

@@ -77,7 +77,7 @@ int gbnn_adam(float *param, const float *grad, float *m, float *v, void *param_b
  * sin(phase), cos(phase), x/W, y/H, 0, 0.  solid: DEVICE uint8 [H][W]. */
 int gbnn_encode_input(const uint8_t *solid, float re_feature, float phase, int H, int W, void *x, void *stream);
 
-/* Training target [P][3] = ((rho - 1)/rho_scale, u/U, v/U) from DEVICE float
+/* Training target [P][3] = ((rho - 1)/rho_scale, u/U - 1, v/U) from DEVICE float
  * fields, and per-pixel loss weight (1 on fluid, 0 on solid; may be NULL). */
 int gbnn_encode_target(const float *rho, const float *u, const float *v, const uint8_t *solid, long long P, float U,
                        float rho_scale, float *target, float *weight, void *stream);

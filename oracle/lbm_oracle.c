@@ -67,7 +67,7 @@ static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
-enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_WALLS = 3, ORC_Y_MOVING = 4 };
+enum { ORC_Y_FREESLIP = 0, ORC_Y_PERIODIC = 1, ORC_Y_ZOUHE = 2, ORC_Y_MOVING = 3, ORC_Y_WALLS = 4 };
 enum { ORC_X_INOUT = 0, ORC_X_PERIODIC = 1 };
 
 /* Eq. 6: the MRT transformation matrix M as printed (rows: rho, e, epsilon,

@@ -24,7 +24,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(BUILD_DIR, "liblbm_oracle.so")
 
-Y_FREESLIP, Y_PERIODIC, Y_ZOUHE, Y_WALLS, Y_MOVING = 0, 1, 2, 3, 4
+Y_FREESLIP, Y_PERIODIC, Y_ZOUHE, Y_MOVING, Y_WALLS = 0, 1, 2, 3, 4
 X_INOUT, X_PERIODIC = 0, 1
 
 _lib = None

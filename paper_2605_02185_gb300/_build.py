@@ -23,6 +23,11 @@ LIB = os.path.join(OUT_DIR, "libgblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills", f"-I{INCLUDE}", f"-I{CSRC}"]
+# The lattice kernels (lbm_k_*.cu) are compiled without multiply-add
+# contraction: every multiply-add in them is written out (fma()), so each
+# node's arithmetic is the same in every kernel however the compiler hoists
+# or inlines, and the step kernels agree bit for bit.
+LATTICE_KERNEL_FLAGS = ["-fmad=false"]
 
 
 def nvcc() -> str:
@@ -55,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
-        cmd = [nv, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        own = LATTICE_KERNEL_FLAGS if os.path.basename(src).startswith("lbm_k_") else []
+        cmd = [nv, *ARCH, *NVCC_FLAGS, *own, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -83,7 +83,7 @@ int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
     const int occ = c->ops->occupancy(shape);
     if (occ <= 0) return LBM_ERR_ARG;
     ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
-    seg = kTmaShapes[shape].ncw * 32 * kTmaShapes[shape].cpt;
+    seg = c->ops->tma_pair * kTmaShapes[shape].ncw * 32 * kTmaShapes[shape].cpt;
   }
   const int nseg = (c->nx + seg - 1) / seg;
   StepParams &p = c->p;

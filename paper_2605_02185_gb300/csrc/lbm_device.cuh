@@ -42,7 +42,7 @@ __host__ __device__ inline double ref_pop(int k, double U) {
   return WD(k) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * U * U);
 }
 
-enum { BC_FREESLIP = 0, BC_PERIODIC = 1, BC_ZOUHE = 2 };
+enum { BC_FREESLIP = 0, BC_PERIODIC = 1, BC_ZOUHE = 2, BC_MOVINGWALL = 3 };
 
 // link-map bits: bit k (1..8) = the pull source x - c_k is solid; bit 15 = solid node
 constexpr uint32_t LM_SOLID = 1u << 15;
@@ -53,21 +53,39 @@ constexpr unsigned ERR_UNSTABLE = 1u;
 constexpr unsigned ERR_TIMEOUT = 2u;
 
 // ---- storage conversion --------------------------------------------------
+// C: arithmetic type of one node; ld2/st2 move the values of two adjacent
+// nodes (x even, so the 2-element access is aligned) as one float2 -- for the
+// 16-bit types one 32-bit word, converted by packed instructions, rounding
+// each half to nearest even exactly as st() does.
 template <class S> struct Store;
 template <> struct Store<float> {
   using C = float;
   __device__ static __forceinline__ C ld(float v) { return v; }
   __device__ static __forceinline__ float st(C v) { return v; }
+  __device__ static __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+  __device__ static __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 template <> struct Store<__half> {
   using C = float;
   __device__ static __forceinline__ C ld(__half v) { return __half2float(v); }
   __device__ static __forceinline__ __half st(C v) { return __float2half_rn(v); }
+  __device__ static __forceinline__ float2 ld2(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+  }
+  __device__ static __forceinline__ void st2(__half *p, float2 v) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
+  }
 };
 template <> struct Store<__nv_bfloat16> {
   using C = float;
   __device__ static __forceinline__ C ld(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __forceinline__ __nv_bfloat16 st(C v) { return __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  }
+  __device__ static __forceinline__ void st2(__nv_bfloat16 *p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+  }
 };
 template <> struct Store<double> {
   using C = double;
@@ -129,14 +147,23 @@ __device__ __forceinline__ bool plain_span(const StepParams &p, int xa, int xb, 
 // A source outside the lattice yields the node's own h*_k (placeholder, later
 // overwritten by a boundary rule); a solid source yields the node's own
 // f*_opp(k), i.e. h*_opp(k) + r_opp(k) - r_k = h*_opp(k) - 6 w_k c_kx U
-// (half-way bounce-back, reflected within the step).  Regular sources come
-// from fetch(k, sx, sy) -- a staged row tile or HBM.
+// (half-way bounce-back, reflected within the step).  With moving walls
+// (Eq. 11, wall velocity (U, 0)) a source above the top row or below the
+// bottom row yields f*_opp(k) - 2 w rho (c_opp(k) . u_w) / c_s^2 of the node
+// itself, on h: h*_opp(k) + 6 w_k c_kx U (rho - 1) with rho the density of the
+// node's f*.  Regular sources come from fetch(k, sx, sy) -- a staged row tile
+// or HBM.
 template <class S, class Fetch>
 __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &p, int xe, int y, uint32_t lm,
                                      Fetch fetch, typename Store<S>::C h[9]) {
   using C = typename Store<S>::C;
   const size_t own = (size_t)y * p.pitch + xe;
   const C U = (C)p.U;
+  C drho_own = (C)0;
+  if (p.bc == BC_MOVINGWALL && (y == 0 || y == p.ny - 1)) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) drho_own += Store<S>::ld(A[(size_t)k * p.plane + own]);
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int sx = xe - CX(k);
@@ -148,7 +175,10 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
       inside = inside && (unsigned)sy < (unsigned)p.ny;
     }
     if (!inside) {
-      h[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
+      if (CY(k) != 0 && p.bc == BC_MOVINGWALL && (unsigned)sy >= (unsigned)p.ny)
+        h[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]) + (C)(6.0 * WD(k) * CX(k)) * U * drho_own;
+      else
+        h[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
     } else if (lm & (1u << k)) {
       h[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
       if (CX(k) != 0) h[k] += (C)(-6.0 * WD(k) * CX(k)) * U;
@@ -166,7 +196,7 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
 template <class C>
 __device__ __forceinline__ void boundaries(C h[9], int xe, int y, const StepParams &p) {
   const C U = (C)p.U;
-  if (p.bc != BC_PERIODIC) {
+  if (p.bc == BC_FREESLIP || p.bc == BC_ZOUHE) {  // periodic and moving walls: done in pull()
     if (y == p.ny - 1) {
       if (p.bc == BC_FREESLIP) {  // Eq. 7a: f5 = f3, f8 = f7, f9 = f6
         h[4] = h[2];
@@ -205,40 +235,156 @@ __device__ __forceinline__ void boundaries(C h[9], int xe, int y, const StepPara
   }
 }
 
+// ---- lane arithmetic -------------------------------------------------------
+// The collisions are written once over a lane type: LF (one node, float),
+// LD (one node, double) or LF2 (two nodes in packed FP32 instructions,
+// FADD2 / FMUL2 / FFMA2).  Every operator rounds on its own and a
+// multiply-add happens only where fma() is written, so each node of an LF2
+// lane gets bit for bit what the LF lane computes for it: kernels may treat a
+// node alone or in a pair and agree exactly.
+struct LF { float v; };
+struct LD { double v; };
+struct LF2 { float2 v; };
+template <class C> struct LaneOf;
+template <> struct LaneOf<float> { using T = LF; };
+template <> struct LaneOf<double> { using T = LD; };
+template <class S> using Lane = typename LaneOf<typename Store<S>::C>::T;
+
+__device__ __forceinline__ LF operator+(LF a, LF b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ LF operator-(LF a, LF b) { return {__fsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ LF operator*(LF a, LF b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ LF fma(LF a, LF b, LF c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ LD operator+(LD a, LD b) { return {__dadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ LD operator-(LD a, LD b) { return {__dsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ LD operator*(LD a, LD b) { return {__dmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ LD fma(LD a, LD b, LD c) { return {__fma_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ LF2 operator+(LF2 a, LF2 b) { return {__fadd2_rn(a.v, b.v)}; }
+// a - b as b * (-1) + a: the product is exact, so this is the correctly
+// rounded difference, the same bits as __fsub_rn.
+__device__ __forceinline__ LF2 operator-(LF2 a, LF2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ LF2 operator*(LF2 a, LF2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ LF2 fma(LF2 a, LF2 b, LF2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+
+// Negated reciprocal -1/x of a density (close to 1).  Float lanes: the
+// hardware estimate y of -1/x refined by one Newton-Raphson step,
+// e = 1 + x y, y' = y + y e, whose error is below one ulp; the refinement
+// runs in lane arithmetic, so a pair reproduces the single lane.  Double: the
+// correctly rounded quotient.  The collisions use -1/x so that no lane
+// negation is needed.
+__device__ __forceinline__ float rcp_estimate(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ LF neg_recip(LF x) {
+  const LF y{rcp_estimate(-x.v)};
+  const LF e = fma(x, y, LF{1.f});
+  return fma(y, e, y);
+}
+__device__ __forceinline__ LF2 neg_recip(LF2 x) {
+  const LF2 y{make_float2(rcp_estimate(-x.v.x), rcp_estimate(-x.v.y))};
+  const LF2 e = fma(x, y, LF2{make_float2(1.f, 1.f)});
+  return fma(y, e, y);
+}
+__device__ __forceinline__ LD neg_recip(LD x) { return {-1.0 / x.v}; }
+
+template <class L> __device__ __forceinline__ L splat(double c);
+template <> __device__ __forceinline__ LF splat<LF>(double c) { return {(float)c}; }
+template <> __device__ __forceinline__ LD splat<LD>(double c) { return {c}; }
+template <> __device__ __forceinline__ LF2 splat<LF2>(double c) { return {make_float2((float)c, (float)c)}; }
+
+// |u|^2 <= 0.09 in every node of the lane (false for NaN).
+__device__ __forceinline__ bool speed_ok(LF uu) { return uu.v <= 0.09f; }
+__device__ __forceinline__ bool speed_ok(LD uu) { return uu.v <= 0.09; }
+__device__ __forceinline__ bool speed_ok(LF2 uu) { return (uu.v.x <= 0.09f) & (uu.v.y <= 0.09f); }
+
+// Per-launch constants of the collision, rounded once from the double
+// parameters (omega = 1/tau).  omega and 1 - omega are chosen so that both
+// are exact in the lane's precision and sum to exactly 1 (Sterbenz: x - y is
+// exact for y/2 <= x <= 2y): the BGK update (1 - omega) h + omega h_eq then
+// carries mass and momentum over without a systematic bias from rounding
+// omega.
+template <class T>
+__device__ __forceinline__ void relaxation_pair(double omega, T &om, T &omc) {
+  om = (T)omega;
+  if (om >= (T)0.5) {
+    omc = (T)1 - om;
+  } else {
+    omc = (T)(1.0 - omega);
+    om = (T)1 - omc;
+  }
+}
+template <class L>
+struct Coef {
+  L U, nUU;                 // U, -U^2
+  L om, omc;                // omega, 1 - omega (exact pair)
+  L w36, w9, w2, w4;        // omega/36, omega/9, omega/2, omega/4
+  L se36, seps36, sq12;     // MRT: s_e/36, s_eps/36, s_q/12
+};
+template <class L> struct LaneScalar { using T = float; };  // LF, LF2
+template <> struct LaneScalar<LD> { using T = double; };
+template <class L>
+__device__ __forceinline__ Coef<L> make_coef(const StepParams &p) {
+  using T = typename LaneScalar<L>::T;
+  T omt, omct;
+  relaxation_pair<T>(p.omega, omt, omct);
+  const double om = omt, omc = omct;
+  Coef<L> k;
+  k.U = splat<L>(p.U);
+  k.nUU = splat<L>(-p.U * p.U);
+  k.om = splat<L>(om);
+  k.omc = splat<L>(omc);
+  k.w36 = splat<L>(om / 36.0);
+  k.w9 = splat<L>(om / 9.0);
+  k.w2 = splat<L>(0.5 * om);
+  k.w4 = splat<L>(0.25 * om);
+  k.se36 = splat<L>(p.s_e / 36.0);
+  k.seps36 = splat<L>(p.s_eps / 36.0);
+  k.sq12 = splat<L>(p.s_q / 12.0);
+  return k;
+}
+
 // BGK collision (Eq. 2) towards Eq. 3 with the moments of Eq. 4, on h.
 // delta_rho = sum h, j = (U, 0) + dj with dj = sum h c, and
 //   h_eq_k = w_k [delta_rho + 3 c.dj + (9/2 ((c.dj)(c.j + c.U) - delta_rho (c.U)^2)
 //            - 3/2 (dj.(j + U) - delta_rho U^2)) / rho],
-// which is f_eq_k(rho, j) - r_k written without cancellation.  Returns |u|^2.
-template <class C>
-__device__ __forceinline__ C collide(C h[9], C omega, C U) {
-  const C drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-  const C djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  const C djy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
-  const C jx = U + djx, jy = djy;
-  const C inv = (C)1 / ((C)1 + drho);
-  const C uu2 = drho * U * U;
-  const C q = (C)1.5 * ((djx * (jx + U) + djy * jy) - uu2) * inv;
-  C heq[9];
+// which is f_eq_k(rho, j) - r_k written without cancellation.  Opposite
+// diagonals share (c.dj)(c.j + c.U).  The relaxation is
+// h* = (1 - omega) h + omega h_eq with omega folded into the equilibrium's
+// factors.  Returns |u|^2.
+template <class L>
+__device__ __forceinline__ L collide(L h[9], const Coef<L> &k) {
+  const L drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const L djx = ((h[1] - h[3]) + (h[5] - h[6])) + (h[8] - h[7]);
+  const L djy = ((h[2] - h[4]) + (h[5] - h[8])) + (h[6] - h[7]);
+  const L jx = k.U + djx, jxU = jx + k.U;
+  const L ninv = neg_recip(splat<L>(1.0) + drho);  // -1/rho
+  const L nuu2 = drho * k.nUU;
+  const L a = djx * jxU, b = djy * djy;
+  const L i45 = ninv * splat<L>(-4.5);
+  const L dq = fma((a + b) + nuu2, ninv * splat<L>(1.5), drho);
+  const L s5 = djx + djy, s6 = djy - djx, t5 = jxU + djy, t6 = djy - jxU;
+  const L A5 = fma(fma(s5, t5, nuu2), i45, dq);
+  const L A6 = fma(fma(s6, t6, nuu2), i45, dq);
+  L o[9];
+  o[5] = fma(splat<L>(3.0), s5, A5) * k.w36;
+  o[7] = fma(splat<L>(-3.0), s5, A5) * k.w36;
+  o[6] = fma(splat<L>(3.0), s6, A6) * k.w36;
+  o[8] = fma(splat<L>(-3.0), s6, A6) * k.w36;
+  // Axis pairs: even parts from Eq. 3, odd parts and the rest population
+  // from exact momentum and mass balance.
+  const L ex = fma(a + nuu2, i45, dq) * k.w9;
+  const L ey = fma(b, i45, dq) * k.w9;
+  const L ox = fma(splat<L>(-0.5), (o[5] - o[6]) + (o[8] - o[7]), djx * k.w2);
+  const L oy = fma(splat<L>(-0.5), (o[5] + o[6]) - (o[7] + o[8]), djy * k.w2);
+  o[1] = ex + ox;
+  o[3] = ex - ox;
+  o[2] = ey + oy;
+  o[4] = ey - oy;
+  o[0] = drho * k.om - (((o[1] + o[3]) + (o[2] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
 #pragma unroll
-  for (int k = 5; k < 9; ++k) {
-    const C cdj = (C)CX(k) * djx + (C)CY(k) * djy;
-    const C cj = (C)CX(k) * jx + (C)CY(k) * jy;
-    const C cU = (C)CX(k) * U;
-    heq[k] = (C)(1.0 / 36.0) * (drho + (C)3 * cdj + ((C)4.5 * (cdj * (cj + cU) - uu2) * inv - q));
-  }
-  const C ex = (C)(2.0 / 9.0) * (drho + ((C)4.5 * (djx * (jx + U) - uu2) * inv - q));
-  const C ey = (C)(2.0 / 9.0) * (drho + ((C)4.5 * (djy * jy) * inv - q));
-  const C ox = djx - ((heq[5] - heq[6]) + (heq[8] - heq[7]));
-  const C oy = djy - ((heq[5] + heq[6]) - (heq[7] + heq[8]));
-  heq[1] = (C)0.5 * (ex + ox);
-  heq[3] = (C)0.5 * (ex - ox);
-  heq[2] = (C)0.5 * (ey + oy);
-  heq[4] = (C)0.5 * (ey - oy);
-  heq[0] = drho - (((heq[1] + heq[3]) + (heq[2] + heq[4])) + ((heq[5] + heq[6]) + (heq[7] + heq[8])));
-#pragma unroll
-  for (int k = 0; k < 9; ++k) h[k] = h[k] + omega * (heq[k] - h[k]);
-  return (jx * jx + jy * jy) * inv * inv;
+  for (int i = 0; i < 9; ++i) h[i] = fma(k.omc, h[i], o[i]);
+  return fma(jx, jx, b) * (ninv * ninv);
 }
 
 // MRT collision (Eq. 6) on h.  The moments of h use the integer rows of M;
@@ -247,50 +393,52 @@ __device__ __forceinline__ C collide(C h[9], C omega, C U) {
 // update h* = h - M^T diag(s_k / |row_k|^2) d leaves rho and j untouched
 // exactly, because the conserved deviations are zero and M is integer.
 // Returns |u|^2.
-template <class C>
-__device__ __forceinline__ C collide_mrt(C h[9], C omega, C U, C se, C seps, C sq) {
-  const C drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-  const C djx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-  const C djy = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
-  const C axis = (h[1] + h[2]) + (h[3] + h[4]);
-  const C diag = (h[5] + h[6]) + (h[7] + h[8]);
-  const C me = (C)2 * diag - axis - (C)4 * h[0];
-  const C meps = (C)4 * h[0] - (C)2 * axis + diag;
-  const C mqx = ((h[5] - h[6]) + (h[8] - h[7])) - (C)2 * (h[1] - h[3]);
-  const C mqy = ((h[5] + h[6]) - (h[7] + h[8])) - (C)2 * (h[2] - h[4]);
-  const C mpxx = (h[1] + h[3]) - (h[2] + h[4]);
-  const C mpxy = (h[5] - h[6]) + (h[7] - h[8]);
-  const C jx = U + djx, jy = djy;
-  const C inv = (C)1 / ((C)1 + drho);
-  const C uu2 = drho * U * U;
-  const C a = djx * (jx + U);
-  const C Q = ((a + djy * jy) - uu2) * inv;
-  const C ce = se * (C)(1.0 / 36.0) * ((me + (C)2 * drho) - (C)3 * Q);
-  const C cps = seps * (C)(1.0 / 36.0) * ((meps - drho) + (C)3 * Q);
-  const C cqx = sq * (C)(1.0 / 12.0) * (mqx + djx);
-  const C cqy = sq * (C)(1.0 / 12.0) * (mqy + djy);
-  const C cxx = omega * (C)0.25 * (mpxx - ((a - djy * jy) - uu2) * inv);
-  const C cxy = omega * (C)0.25 * (mpxy - jx * jy * inv);
-  const C ax = ce + (C)2 * cps;   // common part of the axis directions
-  const C dg = (C)2 * ce + cps;   // common part of the diagonals
-  h[0] -= (C)4 * (cps - ce);
-  h[1] -= ((C)(-2) * cqx + cxx) - ax;
-  h[2] -= ((C)(-2) * cqy - cxx) - ax;
-  h[3] -= ((C)2 * cqx + cxx) - ax;
-  h[4] -= ((C)2 * cqy - cxx) - ax;
-  h[5] -= dg + ((cqx + cqy) + cxy);
-  h[6] -= dg + ((cqy - cqx) - cxy);
-  h[7] -= dg - ((cqx + cqy) - cxy);
-  h[8] -= dg + ((cqx - cqy) - cxy);
-  return (jx * jx + jy * jy) * inv * inv;
+template <class L>
+__device__ __forceinline__ L collide_mrt(L h[9], const Coef<L> &k) {
+  const L drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  const L d13 = h[1] - h[3], d24 = h[2] - h[4];
+  const L d56 = h[5] - h[6], d87 = h[8] - h[7], d58 = h[5] - h[8], d67 = h[6] - h[7];
+  const L djx = (d13 + d56) + d87;
+  const L djy = (d24 + d58) + d67;
+  const L axis = (h[1] + h[2]) + (h[3] + h[4]);
+  const L diag = (h[5] + h[6]) + (h[7] + h[8]);
+  const L me = fma(splat<L>(-4.0), h[0], diag + diag) - axis;
+  const L meps = fma(splat<L>(4.0), h[0], diag) - (axis + axis);
+  const L mqx = fma(splat<L>(-2.0), d13, d56 + d87);
+  const L mqy = fma(splat<L>(-2.0), d24, (h[5] + h[6]) - (h[7] + h[8]));
+  const L mpxx = (h[1] + h[3]) - (h[2] + h[4]);
+  const L mpxy = d56 - d87;
+  const L jx = k.U + djx;
+  const L ninv = neg_recip(splat<L>(1.0) + drho);  // -1/rho
+  const L nuu2 = drho * k.nUU;
+  const L a = djx * (jx + k.U), b = djy * djy;
+  const L nQ = ((a + b) + nuu2) * ninv;  // -Q
+  const L ce = fma(splat<L>(3.0), nQ, fma(splat<L>(2.0), drho, me)) * k.se36;
+  const L cps = fma(splat<L>(-3.0), nQ, meps - drho) * k.seps36;
+  const L cqx = (mqx + djx) * k.sq12;
+  const L cqy = (mqy + djy) * k.sq12;
+  const L cxx = fma((a - b) + nuu2, ninv, mpxx) * k.w4;
+  const L cxy = fma(jx * djy, ninv, mpxy) * k.w4;
+  const L ax = fma(splat<L>(2.0), cps, ce);  // common part of the axis directions
+  const L dg = fma(splat<L>(2.0), ce, cps);  // common part of the diagonals
+  h[0] = fma(splat<L>(-4.0), cps - ce, h[0]);
+  h[1] = h[1] - (fma(splat<L>(-2.0), cqx, cxx) - ax);
+  h[2] = h[2] + (fma(splat<L>(2.0), cqy, cxx) + ax);
+  h[3] = h[3] - (fma(splat<L>(2.0), cqx, cxx) - ax);
+  h[4] = h[4] + (fma(splat<L>(-2.0), cqy, cxx) + ax);
+  h[5] = h[5] - (dg + ((cqx + cqy) + cxy));
+  h[6] = h[6] - (dg + ((cqy - cqx) - cxy));
+  h[7] = h[7] - (dg - ((cqx + cqy) - cxy));
+  h[8] = h[8] - (dg + ((cqx - cqy) - cxy));
+  return fma(jx, jx, b) * (ninv * ninv);
 }
 
 // The collision of model MRT (0: BGK, 1: MRT), a compile-time choice so each
 // step kernel carries only its own collision.
-template <int MRT, class C>
-__device__ __forceinline__ C collide_model(C h[9], const StepParams &p, C omega, C U) {
-  if (MRT) return collide_mrt<C>(h, omega, U, (C)p.s_e, (C)p.s_eps, (C)p.s_q);
-  return collide<C>(h, omega, U);
+template <int MRT, class L>
+__device__ __forceinline__ L collide_model(L h[9], const Coef<L> &k) {
+  if (MRT) return collide_mrt<L>(h, k);
+  return collide<L>(h, k);
 }
 
 // h part of the Eq. 14 link sum for one node: sum over directions i pointing

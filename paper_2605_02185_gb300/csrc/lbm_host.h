@@ -45,7 +45,7 @@ inline int check_opts(const lbm_opts *o) {
   if ((long long)o->nx * o->ny > (1ll << 31) - 1) return LBM_ERR_ARG;
   if (!(o->tau > 0.5) || !std::isfinite(o->tau)) return LBM_ERR_ARG;
   if (!(o->U >= 0.0 && o->U < 0.3)) return LBM_ERR_ARG;
-  if (o->bc_top_bottom < LBM_BC_FREESLIP || o->bc_top_bottom > LBM_BC_ZOUHE) return LBM_ERR_ARG;
+  if (o->bc_top_bottom < LBM_BC_FREESLIP || o->bc_top_bottom > LBM_BC_MOVINGWALL) return LBM_ERR_ARG;
   if (!elem_size(o->storage)) return LBM_ERR_ARG;
   if (o->kernel < LBM_KERNEL_AUTO || o->kernel > LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
   if (o->collision != LBM_COLLIDE_BGK && o->collision != LBM_COLLIDE_MRT) return LBM_ERR_ARG;

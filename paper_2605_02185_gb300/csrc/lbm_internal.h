@@ -38,6 +38,9 @@ struct KernelOps {
   cudaError_t (*bulk_prep)(int shape);
   int (*bulk_occupancy)(int shape);
   size_t (*bulk_smem)(int shape);
+  // nodes per thread and chunk of the single-lattice TMA kernel: its row
+  // tile is tma_pair * warps * 32 * cells-per-thread nodes wide
+  int tma_pair;
 };
 
 const KernelOps *ops_f32();

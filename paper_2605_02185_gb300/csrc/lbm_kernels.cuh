@@ -44,12 +44,26 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
   return y >= p.fy0 && y <= p.fy1 && s >= p.fs0 && s <= p.fs1;
 }
 
+// Collision of one node held in C values (Eq. 2 or Eq. 6); false when the
+// node's speed left the stable range.
+template <int MRT, class S>
+__device__ __forceinline__ bool collide_node(typename Store<S>::C (&h)[9], const Coef<Lane<S>> &cf) {
+  using L = Lane<S>;
+  L v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = L{h[k]};
+  const bool ok = speed_ok(collide_model<MRT, L>(v, cf));
+#pragma unroll
+  for (int k = 0; k < 9; ++k) h[k] = v[k].v;
+  return ok;
+}
+
 // One node, general form: pull (with bounce-back and placeholders), boundary
 // rules, collision into h; adds the node's links to the force.
 template <int MRT, class S, class Fetch>
 __device__ __forceinline__ void node_compute(const S *__restrict__ A, const StepParams &p, int x, int y,
-                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
-                                             double &fx, double &fy, bool &bad, typename Store<S>::C (&h)[9]) {
+                                             const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
+                                             bool &bad, typename Store<S>::C (&h)[9]) {
   using C = typename Store<S>::C;
   const int xe = (x == p.nx - 1) ? p.nx - 2 : x;  // Eq. 13: outlet = column nx-2
   const uint32_t lm = link_mask(p, xe, y);
@@ -59,8 +73,7 @@ __device__ __forceinline__ void node_compute(const S *__restrict__ A, const Step
   } else {
     pull<S>(A, p, xe, y, lm, fetch, h);
     boundaries<C>(h, xe, y, p);
-    const C uu = collide_model<MRT, C>(h, p, omega, U);
-    bad |= !(uu <= (C)0.09);
+    bad |= !collide_node<MRT, S>(h, cf);
     if ((lm & LM_LINKS) && x == xe) link_force<C>(h, lm, fx, fy);
   }
 }
@@ -68,14 +81,11 @@ __device__ __forceinline__ void node_compute(const S *__restrict__ A, const Step
 // One interior fluid node away from every boundary and link (plain_span):
 // every source is regular, no rule applies.
 template <int MRT, class S, class Fetch>
-__device__ __forceinline__ void plain_compute(const StepParams &p, int x, int y, typename Store<S>::C omega,
-                                              typename Store<S>::C U, Fetch fetch, bool &bad,
-                                              typename Store<S>::C (&h)[9]) {
-  using C = typename Store<S>::C;
+__device__ __forceinline__ void plain_compute(const StepParams &p, int x, int y, const Coef<Lane<S>> &cf,
+                                              Fetch fetch, bool &bad, typename Store<S>::C (&h)[9]) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) h[k] = fetch(k, x - CX(k), y - CY(k));
-  const C uu = collide_model<MRT, C>(h, p, omega, U);
-  bad |= !(uu <= (C)0.09);
+  bad |= !collide_node<MRT, S>(h, cf);
 }
 
 template <class S>
@@ -88,20 +98,39 @@ __device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &
 
 template <int MRT, class S, class Fetch>
 __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
-                                            int y, typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
-                                            double &fx, double &fy, bool &bad) {
+                                            int y, const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
+                                            bool &bad) {
   typename Store<S>::C h[9];
-  node_compute<MRT, S>(A, p, x, y, omega, U, fetch, fx, fy, bad, h);
+  node_compute<MRT, S>(A, p, x, y, cf, fetch, fx, fy, bad, h);
   store_node<S>(B, p, x, y, h);
 }
 
 template <int MRT, class S, class Fetch>
 __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams &p, int x, int y,
-                                             typename Store<S>::C omega, typename Store<S>::C U, Fetch fetch,
-                                             bool &bad) {
+                                             const Coef<Lane<S>> &cf, Fetch fetch, bool &bad) {
   typename Store<S>::C h[9];
-  plain_compute<MRT, S>(p, x, y, omega, U, fetch, bad, h);
+  plain_compute<MRT, S>(p, x, y, cf, fetch, bad, h);
   store_node<S>(B, p, x, y, h);
+}
+
+// Two adjacent interior nodes (x even) of a plain span, from a staged row
+// tile (tile[k * seg + x'] = h*_k at column x' of row y - c_ky): the
+// x-aligned planes are read as one pair, the x-shifted ones per node; the
+// collision runs on packed FP32 pairs; each plane is stored as one pair.
+template <int MRT, class S>
+__device__ __forceinline__ void update_pair(S *__restrict__ B, const StepParams &p, int x, int y,
+                                            const Coef<LF2> &cf, const S *__restrict__ tile, int seg, bool &bad) {
+  LF2 h[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const S *src = tile + k * seg + (x - CX(k));
+    if (CX(k) == 0) h[k] = LF2{Store<S>::ld2(src)};
+    else h[k] = LF2{make_float2(Store<S>::ld(src[0]), Store<S>::ld(src[1]))};
+  }
+  bad |= !speed_ok(collide_model<MRT, LF2>(h, cf));
+  S *o = B + (size_t)y * p.pitch + x;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Store<S>::st2(o + (size_t)k * p.plane, h[k].v);
 }
 
 // ---- direct kernel: one CTA per row tile, loads straight from HBM -------
@@ -114,7 +143,7 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   const int y = t / p.nseg, s = t - y * p.nseg;
   const int x0 = s * p.seg;
   const int x1 = min(x0 + p.seg, p.nx);
-  const C omega = (C)p.omega, U = (C)p.U;
+  const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
   double fx = 0.0, fy = 0.0;
   bool bad = false;
   auto fetch = [&](int k, int sx, int sy) -> C {
@@ -123,14 +152,19 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
     if (plain_span(p, xw, xw + 31, y))
-      update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
+      update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
     else if (x < x1)
-      update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+      update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))
     post_force<NT / 32>(p, y, s, fx, fy, (int)threadIdx.x, red, s_last, [] { __syncthreads(); });
 }
+
+// Nodes per thread and chunk in the plain spans of the TMA kernel: pairs of
+// adjacent nodes for the 16-bit storage forms (one 32-bit load and store per
+// aligned plane and pair, packed FP32 arithmetic), single nodes otherwise.
+template <class S> struct TmaPair { static constexpr int nodes = sizeof(S) == 2 ? 2 : 1; };
 
 // ---- TMA-staged persistent kernel ----------------------------------------
 // CTA = NCW compute warps + 1 producer warp.  The producer's elected lane
@@ -144,9 +178,10 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
 template <class S, int NCW, int CPT, int STAGES, int MRT>
 __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
   using C = typename Store<S>::C;
+  constexpr int PX = TmaPair<S>::nodes;  // adjacent nodes per thread and chunk
   constexpr int H = 16 / (int)sizeof(S);
   constexpr int NC = NCW * 32;
-  constexpr int W = NC * CPT;
+  constexpr int W = NC * CPT * PX;
   constexpr int SEG = W + 2 * H;
   extern __shared__ __align__(128) unsigned char smem[];
   S *tiles = reinterpret_cast<S *>(smem);
@@ -218,7 +253,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
 
   // ---------------------------------------- compute warps
   const int ctid = threadIdx.x;
-  const C omega = (C)p.omega, U = (C)p.U;
+  const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
+  const Coef<LF2> cf2 = make_coef<LF2>(p);
   bool bad = false;
   int j = 0;
   for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
@@ -239,12 +275,23 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
       auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        const int xw = x0 + c * NC + (ctid & ~31);
-        const int x = xw + lane;
-        if (plain_span(p, xw, xw + 31, y))
-          update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
-        else if (x < p.nx)
-          update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+        const int xw = x0 + (c * NC + (ctid & ~31)) * PX;
+        if constexpr (PX == 2) {
+          const int x = xw + 2 * lane;
+          if (plain_span(p, xw, xw + 63, y)) {
+            update_pair<MRT, S>(B, p, x, y, cf2, tile, SEG, bad);
+          } else {
+#pragma unroll 1
+            for (int e = 0; e < 2; ++e)
+              if (x + e < p.nx) update_node<MRT, S>(A, B, p, x + e, y, cf, fetch, fx, fy, bad);
+          }
+        } else {
+          const int x = xw + lane;
+          if (plain_span(p, xw, xw + 31, y))
+            update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
+          else if (x < p.nx)
+            update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
@@ -279,7 +326,7 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
   const int y = t / p.nseg, s = t - y * p.nseg;
   const int x0 = s * p.seg;
   const int x1 = min(x0 + p.seg, p.nx);
-  const C omega = (C)p.omega, U = (C)p.U;
+  const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
   double fx = 0.0, fy = 0.0;
   bool bad = false;
   auto fetch = [&](int k, int sx, int sy) -> C {
@@ -288,9 +335,9 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
     if (plain_span(p, xw, xw + 31, y))
-      update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
+      update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
     else if (x < x1)
-      update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+      update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))
@@ -306,9 +353,10 @@ template <class S, int NCW, int CPT, int STAGES, int MRT>
 __global__ void __launch_bounds__((NCW + 1) * 32)
     step_tma_batch(const CaseDesc *__restrict__ cases, int ncases, long long nitems, int parity) {
   using C = typename Store<S>::C;
+  constexpr int PX = TmaPair<S>::nodes;
   constexpr int H = 16 / (int)sizeof(S);
   constexpr int NC = NCW * 32;
-  constexpr int W = NC * CPT;
+  constexpr int W = NC * CPT * PX;
   constexpr int SEG = W + 2 * H;
   extern __shared__ __align__(128) unsigned char smem[];
   S *tiles = reinterpret_cast<S *>(smem);
@@ -411,7 +459,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
     const StepParams &p = cases[c].p;
     const S *__restrict__ A = (const S *)cases[c].buf[parity];
     S *__restrict__ B = (S *)cases[c].buf[parity ^ 1];
-    const C omega = (C)p.omega, U = (C)p.U;
+    const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
     const int x0 = s * W;
     double fx = 0.0, fy = 0.0;
     bool bad = false;
@@ -420,12 +468,23 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
       auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
 #pragma unroll
       for (int cc = 0; cc < CPT; ++cc) {
-        const int xw = x0 + cc * NC + (ctid & ~31);
-        const int x = xw + lane;
-        if (plain_span(p, xw, xw + 31, y))
-          update_plain<MRT, S>(B, p, x, y, omega, U, fetch, bad);
-        else if (x < p.nx)
-          update_node<MRT, S>(A, B, p, x, y, omega, U, fetch, fx, fy, bad);
+        const int xw = x0 + (cc * NC + (ctid & ~31)) * PX;
+        if constexpr (PX == 2) {
+          const int x = xw + 2 * lane;
+          if (plain_span(p, xw, xw + 63, y)) {
+            update_pair<MRT, S>(B, p, x, y, make_coef<LF2>(p), tile, SEG, bad);
+          } else {
+#pragma unroll 1
+            for (int e = 0; e < 2; ++e)
+              if (x + e < p.nx) update_node<MRT, S>(A, B, p, x + e, y, cf, fetch, fx, fy, bad);
+          }
+        } else {
+          const int x = xw + lane;
+          if (plain_span(p, xw, xw + 31, y))
+            update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
+          else if (x < p.nx)
+            update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
@@ -539,7 +598,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
 
   // ---------------------------------------- compute warps
   const int ctid = threadIdx.x;
-  const C omega = (C)p.omega, U = (C)p.U;
+  const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
   bool bad = false;
   int j = 0;
   for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
@@ -565,9 +624,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         const int x = xw + lane;
         C h[9];
         if (plain_span(p, xw, xw + 31, y)) {
-          plain_compute<MRT, S>(p, x, y, omega, U, fetch, bad, h);
+          plain_compute<MRT, S>(p, x, y, cf, fetch, bad, h);
         } else if (x < p.nx) {
-          node_compute<MRT, S>(A, p, x, y, omega, U, fetch, fx, fy, bad, h);
+          node_compute<MRT, S>(A, p, x, y, cf, fetch, fx, fy, bad, h);
         } else {
 #pragma unroll
           for (int k = 0; k < 9; ++k) h[k] = (C)0;
@@ -596,9 +655,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
 }
 
-template <class S, int NCW, int CPT, int STAGES>
+// Dynamic shared memory of a TMA kernel whose row tile holds PX * NCW * 32 *
+// CPT nodes (PX = TmaPair<S>::nodes for step_tma and step_tma_batch).
+template <class S, int NCW, int CPT, int STAGES, int PX = 1>
 constexpr size_t tma_smem_bytes() {
-  return (size_t)STAGES * 9 * (NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t);
+  return (size_t)STAGES * 9 * (PX * NCW * 32 * CPT + 2 * (16 / sizeof(S))) * sizeof(S) + 2 * STAGES * sizeof(uint64_t);
 }
 
 // ---- initial state: f*(0) = f_eq(rho0, u0), Eq. 3, as offsets ----------
@@ -676,8 +737,10 @@ __global__ void init_device_kernel(S *__restrict__ A, StepParams p, const float 
       const double cu = CX(k) * ux + CY(k) * uy;
       double f = WD(k) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
       if (with_noneq) {
+        // stored state is post-collision: f*_neq = (1 - 1/tau) f_neq, and
+        // (1 - 1/tau) (-tau w rho / c_s^2) = -(tau - 1) w rho / c_s^2
         const double qxx = CX(k) * CX(k) - 1.0 / 3.0, qyy = CY(k) * CY(k) - 1.0 / 3.0, qxy = CX(k) * CY(k);
-        f -= 3.0 * tau * WD(k) * r * (qxx * dudx + qyy * dvdy + qxy * (dudy + dvdx));
+        f -= 3.0 * (tau - 1.0) * WD(k) * r * (qxx * dudx + qyy * dvdy + qxy * (dudy + dvdx));
       }
       A[(size_t)k * p.plane + o] = Store<S>::st((typename Store<S>::C)(f - ref_pop(k, p.U)));
     }
@@ -786,7 +849,7 @@ struct Launch {
 
   template <int NCW, int CPT, int STAGES>
   static cudaError_t tma_one(int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
-    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     if (p.mrt)
       step_tma<S, NCW, CPT, STAGES, 1><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
@@ -796,7 +859,7 @@ struct Launch {
   }
   template <int NCW, int CPT, int STAGES>
   static cudaError_t tma_prep() {
-    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const cudaError_t e = cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES, 0>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -806,7 +869,7 @@ struct Launch {
   }
   template <int NCW, int CPT, int STAGES>
   static int tma_occ() {
-    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
     if (smem > 227 * 1024) return 0;
     int n = 0;
     int m = 0;
@@ -852,7 +915,7 @@ struct Launch {
     switch (shape) {
 #define X(id, a, b, c) \
   case id:             \
-    return tma_smem_bytes<S, a, b, c>();
+    return tma_smem_bytes<S, a, b, c, TmaPair<S>::nodes>();
       GBLBM_TMA_SHAPES(X)
 #undef X
     }
@@ -978,7 +1041,7 @@ struct Launch {
   template <int NCW, int CPT, int STAGES>
   static cudaError_t batch_tma_one(int grid, const CaseDesc *cases, int ncases, long long nitems, int parity,
                                    int mrt, cudaStream_t st) {
-    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     if (mrt)
       step_tma_batch<S, NCW, CPT, STAGES, 1><<<grid, (NCW + 1) * 32, smem, st>>>(cases, ncases, nitems, parity);
@@ -988,7 +1051,7 @@ struct Launch {
   }
   template <int NCW, int CPT, int STAGES>
   static cudaError_t batch_tma_prep() {
-    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const cudaError_t e = cudaFuncSetAttribute(step_tma_batch<S, NCW, CPT, STAGES, 0>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1022,7 +1085,8 @@ struct Launch {
     static const KernelOps ops = {(int)sizeof(S), &direct,     &tma,          &prep,     &occupancy,
                                   &smem,          &init,       &force,        &fields,   &mass_rows,
                                   &batch_direct,  &batch_tma,  &batch_prep, &init_device,
-                                  &tma_bulk,      &bulk_prep,  &bulk_occupancy, &bulk_smem};
+                                  &tma_bulk,      &bulk_prep,  &bulk_occupancy, &bulk_smem,
+                                  TmaPair<S>::nodes};
     return &ops;
   }
 };

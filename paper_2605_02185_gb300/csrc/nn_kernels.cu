@@ -252,6 +252,108 @@ __global__ void __launch_bounds__(WG_THREADS) conv_wgrad_kernel(const bf16 *__re
   if (do_bias && tid < WG_BMN && o0 + tid < cout) atomicAdd(gb + o0 + tid, bsum);
 }
 
+// ---- weight gradient, all nine taps per block (32 x 32 channel tiles) ----
+// For the wide, shallow layers (full resolution, <= 32 output channels) the
+// per-tap kernel above re-reads every input row nine times.  Here one block
+// stages a 64-pixel row segment of gy (32 output channels) and the three
+// input rows around it (32 input channels, 1-pixel halo) once, and its nine
+// warps -- one per tap -- each accumulate a 32 x 32 tile of that tap's
+// gradient from shifted views of the staged rows.
+constexpr int W9_PX = 64;
+constexpr int W9_CP = 40;  // padded channel stride (conflict-free ldmatrix rows)
+constexpr int W9_THREADS = 288;
+
+struct W9Smem {
+  bf16 g[W9_PX][W9_CP];              // [pixel][o]
+  bf16 xs[3][W9_PX + 2][W9_CP];      // [row][pixel + halo][c]
+};
+
+__global__ void __launch_bounds__(W9_THREADS) conv_wgrad9_kernel(const bf16 *__restrict__ x, int xs,
+                                                                const bf16 *__restrict__ gy, int gs,
+                                                                float *__restrict__ gw, float *__restrict__ gb, int N,
+                                                                int H, int W, int cin, int cout,
+                                                                long long segs_per_block) {
+  __shared__ __align__(128) W9Smem sm;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tap = warp, dy = tap / 3, dx = tap % 3;
+  const int ncc = (cin + 31) / 32;
+  const int o0 = (blockIdx.y / ncc) * 32, c0 = (blockIdx.y % ncc) * 32;
+  const int spr = (W + W9_PX - 1) / W9_PX;  // segments per image row
+  const long long nsegs = (long long)N * H * spr;
+  const long long s_begin = (long long)blockIdx.x * segs_per_block;
+  const long long s_end = s_begin + segs_per_block < nsegs ? s_begin + segs_per_block : nsegs;
+  const bool do_bias = gb != nullptr && c0 == 0;
+  float bsum = 0.f;
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+  for (long long sg = s_begin; sg < s_end; ++sg) {
+    const int w0 = (int)(sg % spr) * W9_PX;
+    const long long r = sg / spr;
+    const int h = (int)(r % H), n = (int)(r / H);
+    for (int i = tid; i < W9_PX * 4; i += W9_THREADS) {  // gy: 64 pixels x 32 channels
+      const int v = i & 3, px = i >> 2;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (w0 + px < W && o0 + v * 8 < cout)
+        val = *reinterpret_cast<const uint4 *>(gy + (((size_t)n * H + h) * W + w0 + px) * gs + o0 + v * 8);
+      *reinterpret_cast<uint4 *>(&sm.g[px][v * 8]) = val;
+    }
+    for (int i = tid; i < 3 * (W9_PX + 2) * 4; i += W9_THREADS) {  // x: 3 rows x 66 pixels x 32 channels
+      const int v = i & 3, px = (i >> 2) % (W9_PX + 2), rr = (i >> 2) / (W9_PX + 2);
+      const int hh = h + rr - 1, ww = w0 + px - 1;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (hh >= 0 && hh < H && ww >= 0 && ww < W && c0 + v * 8 < cin)
+        val = *reinterpret_cast<const uint4 *>(x + (((size_t)n * H + hh) * W + ww) * xs + c0 + v * 8);
+      *reinterpret_cast<uint4 *>(&sm.xs[rr][px][v * 8]) = val;
+    }
+    __syncthreads();
+    if (do_bias && tid < 32)
+      for (int px = 0; px < W9_PX; ++px) bsum += __bfloat162float(sm.g[px][tid]);
+#pragma unroll
+    for (int kk = 0; kk < W9_PX; kk += 16) {
+      const int q = lane >> 3, rw = lane & 7;
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)  // A = gy^T (m = o, k = pixel), stored [pixel][o]
+        ldsm_x4_t(saddr(&sm.g[kk + (q >> 1) * 8 + rw][mt * 16 + (q & 1) * 8]), a[mt][0], a[mt][1], a[mt][2],
+                  a[mt][3]);
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {  // B = shifted x (k = pixel, n = c), stored [pixel][c]
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(saddr(&sm.xs[dy][kk + (q & 1) * 8 + rw + dx][np * 16 + (q >> 1) * 8]), b0, b1, b2, b3);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_bf16(acc[mt][2 * np], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+          mma_bf16(acc[mt][2 * np + 1], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b2, b3);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int o = o0 + mt * 16 + hf * 8 + g;
+      if (o >= cout) continue;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int c = c0 + nt * 8 + 2 * t;
+        if (c >= cin) continue;
+        float *dst = gw + ((size_t)o * 9 + tap) * cin + c;
+        atomicAdd(dst, acc[mt][nt][2 * hf]);
+        atomicAdd(dst + 1, acc[mt][nt][2 * hf + 1]);
+      }
+    }
+  if (do_bias && tid < 32 && o0 + tid < cout) atomicAdd(gb + o0 + tid, bsum);
+}
+
 // wf[c, dy, dx, o] = w[o, 2-dy, 2-dx, c]
 __global__ void flip_weights_kernel(const bf16 *__restrict__ w, bf16 *__restrict__ wf, int cout, int cin) {
   const long long n = (long long)cout * 9 * cin;
@@ -376,13 +478,15 @@ __global__ void encode_input_kernel(const uint8_t *__restrict__ solid, float re_
   }
 }
 
-// training target [P][3] = ((rho - 1) / rho_scale, u / U, v / U), weight = fluid
+// training target [P][3] = ((rho - 1) / rho_scale, u / U - 1, v / U), weight = fluid;
+// the velocity is taken relative to the free stream so that the network's
+// bfloat16 output resolves the deviations, not the mean flow
 __global__ void encode_target_kernel(const float *__restrict__ rho, const float *__restrict__ u,
                                      const float *__restrict__ v, const uint8_t *__restrict__ solid, long long P,
                                      float U, float rho_scale, float *__restrict__ target, float *__restrict__ weight) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
     target[3 * i] = (rho[i] - 1.f) / rho_scale;
-    target[3 * i + 1] = u[i] / U;
+    target[3 * i + 1] = u[i] / U - 1.f;
     target[3 * i + 2] = v[i] / U;
     if (weight) weight[i] = solid[i] ? 0.f : 1.f;
   }
@@ -395,7 +499,7 @@ __global__ void decode_output_kernel(const bf16 *__restrict__ out, int os, const
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
     const bool s = solid[i] != 0;
     rho[i] = s ? 1.f : 1.f + rho_scale * __bfloat162float(out[i * os]);
-    u[i] = s ? 0.f : U * __bfloat162float(out[i * os + 1]);
+    u[i] = s ? 0.f : U * (1.f + __bfloat162float(out[i * os + 1]));
     v[i] = s ? 0.f : U * __bfloat162float(out[i * os + 2]);
   }
 }
@@ -460,6 +564,16 @@ int gbnn_conv3x3_wgrad(const void *x, int x_cstride, const void *gy, int gy_cstr
     return -1;
   const cudaStream_t st = (cudaStream_t)stream;
   const long long P = (long long)N * H * W;
+  if (cout <= 32) {  // wide, shallow layer: all nine taps per block
+    const long long nsegs = (long long)N * H * ((W + W9_PX - 1) / W9_PX);
+    const int blocks = splits > 0 ? splits : 608;
+    const long long spb = (nsegs + blocks - 1) / blocks;
+    const int nb = (int)((nsegs + spb - 1) / spb);
+    const int ny = ((cout + 31) / 32) * ((cin + 31) / 32);
+    conv_wgrad9_kernel<<<dim3(nb, ny), W9_THREADS, 0, st>>>((const bf16 *)x, x_cstride, (const bf16 *)gy, gy_cstride,
+                                                            gw, gb, N, H, W, cin, cout, spb);
+    return err(cudaGetLastError());
+  }
   if (splits <= 0) splits = 304;
   long long ppb = (P + splits - 1) / splits;
   ppb = (ppb + WG_BK - 1) / WG_BK * WG_BK;

@@ -57,7 +57,12 @@ def _p(t):
 
 
 def _s(stream):
-    return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    """The CUDA stream of a torch stream; None means torch's current stream,
+    so kernels stay ordered with the torch operations around them."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
 
 
 def conv3x3_fwd(x, xs, w, bias, y, ys, N, H, W, cin, cout, relu, mask=None, ms=0, stream=None):
@@ -326,6 +331,22 @@ class WarmStartNet:
         fill_zero(self.loss, stream)
         mse(self.out, self.OUT_C, target, weight, self.g_out, self.OUT_C, P, 3, 1.0 / (3 * P), self.loss, stream)
         return self.loss
+
+    def state(self) -> dict:
+        """Host copy of the FP32 master weights and biases (name -> array)."""
+        out = {}
+        for name, c in self.layers.items():
+            out[name + ".w"] = c.w.detach().cpu().numpy()
+            out[name + ".b"] = c.b.detach().cpu().numpy()
+        return out
+
+    def load_state(self, st: dict, stream=None):
+        """Set the weights from `state()` output and refresh the bfloat16 copies."""
+        import torch
+        for name, c in self.layers.items():
+            c.w.copy_(torch.from_numpy(np.ascontiguousarray(st[name + ".w"])))
+            c.b.copy_(torch.from_numpy(np.ascontiguousarray(st[name + ".b"])))
+            c.sync_bf16(stream, t=0)
 
     def flops_per_sample(self) -> float:
         """Multiply-adds x 2 of the forward convolutions of one sample."""

@@ -36,7 +36,9 @@ class Config:
     re_lo: float = 60.0
     re_hi: float = 200.0
     train_cases: int = 32
-    snapshots: int = 20000
+    snapshots: int = 20000    # snapshots the solver hands to the trainer
+    replay: int = 1024        # snapshots held in the replay buffer (device memory)
+    iters: int = 0            # training iterations; 0: snapshots // batch
     batch: int = 4
     lr: float = 1e-3
     lr_final: float = 1e-4
@@ -47,11 +49,17 @@ class Config:
     collision: int = lbm.LBM_COLLIDE_MRT
     seed: int = 7
     eval_seed: int = 11
-    perturb: float = 1e-3
+    perturb: float = 1e-3     # cold start: seeded +-perturb U velocity noise
+    train_perturb: float = 0.1  # training cases start from a larger kick (earlier shedding onset)
+    rho_factor: float = 8.0   # density target (rho - 1) / (rho_factor U^2)
 
     @property
     def rho_scale(self) -> float:
-        return self.U * self.U
+        return self.rho_factor * self.U * self.U
+
+    @property
+    def train_iters(self) -> int:
+        return self.iters or max(1, self.snapshots // self.batch)
 
 
 def re_values(n: int, seed: int, lo: float, hi: float) -> np.ndarray:
@@ -63,8 +71,9 @@ def re_feature(Re: float, cfg: Config) -> float:
     return 2.0 * (math.log(Re) - math.log(cfg.re_lo)) / (math.log(cfg.re_hi) - math.log(cfg.re_lo)) - 1.0
 
 
-def case_for(Re: float, cfg: Config, seed: int) -> W.Workload:
-    return W.cylinder_case(cfg.D, cfg.U, Re, seed=seed, perturb=cfg.perturb, name=f"ws_D{cfg.D}_Re{Re:.1f}")
+def case_for(Re: float, cfg: Config, seed: int, perturb: float | None = None) -> W.Workload:
+    return W.cylinder_case(cfg.D, cfg.U, Re, seed=seed, perturb=cfg.perturb if perturb is None else perturb,
+                           name=f"ws_D{cfg.D}_Re{Re:.1f}")
 
 
 def phase_now(cl: np.ndarray) -> float | None:
@@ -105,7 +114,7 @@ class SnapshotSource:
         import torch
         self.cfg = cfg
         self.res = re_values(cfg.train_cases, cfg.seed, cfg.re_lo, cfg.re_hi)
-        self.cases = [case_for(Re, cfg, cfg.seed * 1000 + i) for i, Re in enumerate(self.res)]
+        self.cases = [case_for(Re, cfg, cfg.seed * 1000 + i, cfg.train_perturb) for i, Re in enumerate(self.res)]
         self.batch = lbm.Batch(self.cases, collision=cfg.collision, stream=stream, device=device,
                                history_capacity=1 << 20)
         self.batch.init_all()
@@ -141,8 +150,48 @@ class SnapshotSource:
 # ----------------------------------------------------------------- train
 
 
+class Replay:
+    """Ring of labelled training snapshots in device memory: targets
+    ((rho - 1) / rho_scale, u / U - 1, v / U) per node and (Re feature, phase)."""
+
+    def __init__(self, cfg: Config, src: SnapshotSource, device):
+        import torch
+        self.cfg, self.src = cfg, src
+        self.P = src.H * src.W
+        self.cap = cfg.replay
+        self.T = torch.empty((self.cap, self.P, 3), dtype=torch.float32, device=device)
+        self.weight = torch.empty(self.P, dtype=torch.float32, device=device)
+        self.ref = np.zeros(self.cap)
+        self.phase = np.zeros(self.cap)
+        self.fr = [torch.empty((src.H, src.W), dtype=torch.float32, device=device) for _ in range(3)]
+        self.made = 0
+
+    @property
+    def filled(self) -> int:
+        return min(self.made, self.cap)
+
+    def round(self, cases, stream):
+        """Advance the solver `stride` steps and store every case's fields."""
+        cfg, src = self.cfg, self.src
+        src.batch.step(cfg.stride)
+        src.steps += cfg.stride
+        for c in cases:
+            k = self.made % self.cap
+            lbm.lbm_fields_device(src.batch.case(c), *(t.data_ptr() for t in self.fr))
+            nn.encode_target(self.fr[0], self.fr[1], self.fr[2], src.solid, self.P, cfg.U, cfg.rho_scale, self.T[k],
+                             self.weight, stream)
+            self.ref[k] = re_feature(float(src.res[c]), cfg)
+            self.phase[k] = src.phase(c)
+            self.made += 1
+
+
 def train(cfg: Config, device=None, log=print):
     """Generate snapshots with the batched solver and train the network.
+
+    After the spin-up the solver fills a replay ring with snapshots of every
+    periodic case, then keeps stepping between training iterations and
+    overwrites the oldest entries, until `snapshots` have been made; each
+    iteration trains on `batch` entries drawn uniformly from the ring.
     Returns (net, info)."""
     import torch
     device = device or torch.device("cuda")
@@ -152,26 +201,33 @@ def train(cfg: Config, device=None, log=print):
     src.spin_up(log)
     t_spin = time.perf_counter() - t0
     H, Wd, B = src.H, src.W, cfg.batch
-    net = nn.WarmStartNet(B, H, Wd, device, seed=cfg.seed)
-    P1 = H * Wd
-    target = torch.empty((B * P1, 3), dtype=torch.float32, device=device)
-    weight = torch.empty(B * P1, dtype=torch.float32, device=device)
-    fr = [torch.empty((H, Wd), dtype=torch.float32, device=device) for _ in range(3)]
-    iters = max(1, cfg.snapshots // B)
     cases = src.periodic or list(range(len(src.cases)))
-    losses = []
-    t1 = time.perf_counter()
+    P1 = H * Wd
+    rng = np.random.default_rng(cfg.seed)
     with torch.cuda.stream(stream):
+        net = nn.WarmStartNet(B, H, Wd, device, seed=cfg.seed)
+        target = torch.empty((B * P1, 3), dtype=torch.float32, device=device)
+        weight = torch.empty(B * P1, dtype=torch.float32, device=device)
+        rep = Replay(cfg, src, device)
+        t1 = time.perf_counter()
+        while rep.made < min(cfg.replay, cfg.snapshots):
+            rep.round(cases, stream)
+        for j in range(B):
+            weight[j * P1:(j + 1) * P1].copy_(rep.weight)
+        t_fill = time.perf_counter() - t1
+        iters = cfg.train_iters
+        rounds_left = max(0, -(-(cfg.snapshots - rep.made) // len(cases)))
+        losses = []
+        t2 = time.perf_counter()
+        done_rounds = 0
         for it in range(iters):
-            src.batch.step(cfg.stride)
-            src.steps += cfg.stride
-            for j in range(B):
-                c = cases[(it * B + j) % len(cases)]
-                ctx = src.batch.case(c)
-                lbm.lbm_fields_device(ctx, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr())
-                nn.encode_target(fr[0], fr[1], fr[2], src.solid, P1, cfg.U, cfg.rho_scale, target[j * P1:(j + 1) * P1],
-                                 weight[j * P1:(j + 1) * P1], stream)
-                nn.encode_input(src.solid, re_feature(float(src.res[c]), cfg), src.phase(c), H, Wd, net.x0[j], stream)
+            while done_rounds < rounds_left and done_rounds * iters < it * rounds_left:
+                rep.round(cases, stream)
+                done_rounds += 1
+            idx = rng.integers(0, rep.filled, B)
+            for j, k in enumerate(idx):
+                nn.encode_input(src.solid, float(rep.ref[k]), float(rep.phase[k]), H, Wd, net.x0[j], stream)
+                target[j * P1:(j + 1) * P1].copy_(rep.T[k])
             net.forward(stream)
             loss = net.loss_and_grad(target, weight, stream)
             net.backward(stream)
@@ -180,13 +236,13 @@ def train(cfg: Config, device=None, log=print):
             net.adam_step(lr, stream)
             if it % 50 == 0 or it == iters - 1:
                 stream.synchronize()
-                losses.append((it, loss.item()))
+                losses.append((it, loss.item() / (3 * B * P1)))
                 if it % 500 == 0:
-                    log(f"iter {it}/{iters} loss {loss.item():.4e}")
+                    log(f"iter {it}/{iters} loss {losses[-1][1]:.4e} snapshots {rep.made}")
     stream.synchronize()
-    t_train = time.perf_counter() - t1
-    info = {"spinup_s": t_spin, "train_s": t_train, "iters": iters, "snapshots": iters * B,
-            "train_re": [float(r) for r in src.res], "periodic_cases": len(src.periodic),
+    t_train = time.perf_counter() - t2
+    info = {"spinup_s": t_spin, "fill_s": t_fill, "train_s": t_train, "iters": iters, "snapshots": rep.made,
+            "samples_seen": iters * B, "train_re": [float(r) for r in src.res], "periodic_cases": len(src.periodic),
             "losses": losses, "flops_per_sample_fwd": net.flops_per_sample()}
     src.batch.close()
     return net, info

@@ -25,8 +25,8 @@ import math
 
 import numpy as np
 
-BC_FREESLIP, BC_PERIODIC, BC_ZOUHE = 0, 1, 2
-BC_NAMES = {BC_FREESLIP: "freeslip", BC_PERIODIC: "periodic", BC_ZOUHE: "zouhe"}
+BC_FREESLIP, BC_PERIODIC, BC_ZOUHE, BC_MOVINGWALL = 0, 1, 2, 3
+BC_NAMES = {BC_FREESLIP: "freeslip", BC_PERIODIC: "periodic", BC_ZOUHE: "zouhe", BC_MOVINGWALL: "movingwall"}
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)

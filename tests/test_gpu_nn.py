@@ -272,3 +272,44 @@ def test_network_trains_on_a_fixed_target():
         if it % 10 == 0:
             losses.append(loss.item() / (N * H * W * 3))
     assert losses[-1] < 0.2 * losses[0], losses
+
+
+def test_encoders_and_decoder():
+    """Network input channels; targets ((rho - 1)/s, u/U - 1, v/U) with the
+    fluid weight; the decoder inverts the target map of a bfloat16 output."""
+    rng = np.random.default_rng(17)
+    H, W, U, s = 7, 12, 0.05, 8 * 0.05 ** 2
+    P = H * W
+    solid = np.zeros((H, W), np.uint8)
+    solid[3, 4:7] = 1
+    rho = (1 + 0.003 * rng.standard_normal((H, W))).astype(np.float32)
+    u = (U * (1 + 0.2 * rng.standard_normal((H, W)))).astype(np.float32)
+    v = (0.01 * rng.standard_normal((H, W))).astype(np.float32)
+    t_solid = torch.from_numpy(solid).to(DEV)
+    tr, tu, tv = (torch.from_numpy(a).to(DEV) for a in (rho, u, v))
+    target = torch.empty((P, 3), dtype=torch.float32, device=DEV)
+    weight = torch.empty(P, dtype=torch.float32, device=DEV)
+    nn.encode_target(tr, tu, tv, t_solid, P, U, s, target, weight)
+    want = np.stack([(rho - np.float32(1)) / np.float32(s), u / np.float32(U) - np.float32(1), v / np.float32(U)],
+                    -1).reshape(P, 3)
+    np.testing.assert_allclose(target.cpu().numpy(), want, rtol=1e-6, atol=1e-6)
+    assert np.array_equal(weight.cpu().numpy(), 1.0 - solid.reshape(-1))
+    out = torch.zeros((P, 8), dtype=torch.bfloat16, device=DEV)
+    out[:, :3] = target.to(torch.bfloat16)
+    r2, u2, v2 = (torch.empty((H, W), dtype=torch.float32, device=DEV) for _ in range(3))
+    nn.decode_output(out, 8, t_solid, P, U, s, r2, u2, v2)
+    o = out[:, :3].float().cpu().numpy().reshape(H, W, 3)
+    fl = solid == 0
+    np.testing.assert_allclose(r2.cpu().numpy()[fl], (1 + s * o[..., 0])[fl], rtol=1e-6)
+    np.testing.assert_allclose(u2.cpu().numpy()[fl], (U * (1 + o[..., 1]))[fl], rtol=1e-6)
+    np.testing.assert_allclose(v2.cpu().numpy()[fl], (U * o[..., 2])[fl], rtol=1e-6, atol=1e-9)
+    assert np.all(r2.cpu().numpy()[~fl] == 1) and np.all(u2.cpu().numpy()[~fl] == 0)
+    x = torch.empty((H, W, 8), dtype=torch.bfloat16, device=DEV)
+    nn.encode_input(t_solid, 0.25, 1.0, H, W, x)
+    xs = x.float().cpu().numpy()
+    assert np.array_equal(xs[..., 0], solid.astype(np.float32))
+    np.testing.assert_allclose(xs[..., 1], 0.25)
+    np.testing.assert_allclose(xs[..., 2], np.sin(1.0), rtol=4e-3)
+    np.testing.assert_allclose(xs[..., 3], np.cos(1.0), rtol=4e-3)
+    np.testing.assert_allclose(xs[..., 4], np.arange(W)[None, :] / W * np.ones((H, 1)), rtol=4e-3, atol=1e-6)
+    np.testing.assert_allclose(xs[..., 5], np.arange(H)[:, None] / H * np.ones((1, W)), rtol=4e-3, atol=1e-6)

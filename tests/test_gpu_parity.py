@@ -89,7 +89,7 @@ def compare(wl, steps, pops, F, fields, tol_f, tol_F, storage=lbm.LBM_F32, mrt=F
 
 
 KERNELS = [("direct", dict(kernel=lbm.LBM_KERNEL_DIRECT)), ("tma", dict(kernel=lbm.LBM_KERNEL_TMA))]
-BCS = [W.BC_FREESLIP, W.BC_PERIODIC, W.BC_ZOUHE]
+BCS = [W.BC_FREESLIP, W.BC_PERIODIC, W.BC_ZOUHE, W.BC_MOVINGWALL]
 
 
 @pytest.mark.parametrize("kname,kw", KERNELS, ids=[k[0] for k in KERNELS])
@@ -143,6 +143,49 @@ def test_parity_small_cylinder_stable_tau_2000_steps():
     compare(wl, 2000, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4)
 
 
+@pytest.mark.parametrize("storage,tol,tol_F", [(lbm.LBM_F32, 1e-5, 1e-4), (lbm.LBM_F64, 1e-12, 1e-10)],
+                         ids=["f32", "f64"])
+def test_production_case_matches_oracle_every_node(storage, tol, tol_F):
+    """The 3200 x 1600 production case (Re = 100, D = 80, U = 0.05,
+    tau = 0.62, seeded perturbation) after 1000 steps, every node and every
+    force entry against the oracle."""
+    wl = W.PRODUCTION_D80
+    pops, F, fields, _ = gpu_run(wl, 1000, storage=storage)
+    compare(wl, 1000, pops, F, fields, tol_f=tol * wl.U, tol_F=tol_F, storage=storage)
+
+
+@pytest.mark.parametrize("with_noneq", [False, True], ids=["equilibrium", "with_noneq"])
+def test_device_init_matches_oracle(with_noneq):
+    """lbm_init_fields_device: f(0) = f_eq(rho, u) [+ the Chapman-Enskog
+    f_neq(grad u) of the oracle], stored as its collision
+    f*(0) = f_eq + (1 - 1/tau) f_neq; FP64 storage, fluid nodes."""
+    from oracle import conv_oracle as C
+    wl = W.random_case(67, 37, seed=13, bc=W.BC_FREESLIP, D=8, tau=0.56)
+    yy, xx = np.mgrid[0:wl.ny, 0:wl.nx].astype(np.float64)
+    rho = (1.0 + 0.01 * np.sin(0.21 * xx) * np.cos(0.17 * yy)).astype(np.float32)
+    u = (wl.U * (1.0 + 0.3 * np.sin(0.13 * yy + 0.05 * xx))).astype(np.float32)
+    v = (0.02 * np.cos(0.11 * xx - 0.07 * yy)).astype(np.float32)
+    solid = wl.mask().astype(bool)
+    u[solid] = 0.0
+    v[solid] = 0.0
+    lat = lbm.lattice_for(wl, storage=lbm.LBM_F64)
+    try:
+        dev = [torch.from_numpy(a).cuda() for a in (rho, u, v)]
+        lbm.lbm_init_fields_device(lat.h, *(t.data_ptr() for t in dev), with_noneq)
+        lat.sync()
+        pops = lat.get_populations()
+    finally:
+        lat.close()
+    o = O.Oracle(wl.nx, wl.ny, wl.tau, wl.U, bc_y=wl.bc, mask=wl.mask())
+    o.init_equilibrium(rho.astype(np.float64), u.astype(np.float64), v.astype(np.float64))
+    want = o.get_f()
+    if with_noneq:
+        want = want + (1.0 - 1.0 / wl.tau) * C.noneq_populations(rho.astype(np.float64), u.astype(np.float64),
+                                                                  v.astype(np.float64), wl.tau, solid)
+    got = offsets_to_f(pops, wl.U, lbm.LBM_F64)
+    assert np.max(np.abs(got - want)[:, ~solid]) <= 1e-13
+
+
 def test_unstable_case_is_flagged_like_the_oracle():
     """Past its stable span the small cylinder case diverges on both sides;
     the GPU path reports it through lbm_sync instead of returning garbage."""
@@ -184,6 +227,32 @@ def test_mrt_parity_small_cylinder_2000_steps():
     q = 0.5 * wl.U ** 2 * wl.D
     _, Fo, _ = oracle_run(wl, wl.steps, True)
     assert np.max(np.abs(F[:, 0] - Fo[:, 0]) / q) <= 1e-4 * np.max(np.abs(Fo[:, 0]) / q)
+
+
+def test_moving_walls_small_cylinder_mrt():
+    """The C1 geometry (Re = 100, D = 10, 400 x 200, U = 0.1, tau = 0.53) with
+    constant-velocity bounce-back top and bottom (Eq. 11) and the paper's MRT
+    collision: 1000 steps within max |u - u_ref| <= 1e-5 U."""
+    import dataclasses
+    wl = dataclasses.replace(W.PARITY_D10, bc=W.BC_MOVINGWALL, name="cyl_D10_400x200_movingwall")
+    pops, F, fields, _ = gpu_run(wl, 1000, **MRT)
+    compare(wl, 1000, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS], ids=["f16", "bf16"])
+@pytest.mark.parametrize("mrt", [False, True], ids=["bgk", "mrt"])
+def test_paired_16bit_tma_matches_direct(storage, mrt):
+    """The 16-bit TMA kernel updates plain spans two adjacent nodes at a time
+    with packed FP32 instructions and 32-bit loads and stores; every node must
+    still get the bits of the one-node path of the direct kernel."""
+    wl = W.random_case(613, 57, seed=23, bc=W.BC_MOVINGWALL if mrt else W.BC_FREESLIP, D=10)
+    kw = dict(storage=storage, **(MRT if mrt else {}))
+    ref, Fr, _, _ = gpu_run(wl, 30, kernel=lbm.LBM_KERNEL_DIRECT, **kw)
+    for shape in lbm.lbm_kernel_shapes():
+        pops, F, _, info = gpu_run(wl, 30, kernel=lbm.LBM_KERNEL_TMA, shape=shape, **kw)
+        assert (info["consumer_warps"], info["cells_per_thread"], info["stages"]) == shape
+        assert np.array_equal(pops, ref), shape
+        assert np.array_equal(F, Fr), shape
 
 
 def test_every_tma_shape_matches_direct():
