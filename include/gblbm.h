@@ -58,7 +58,8 @@ extern "C" {
  * Populations are stored as offsets h_i = f_i - r_i from the free-stream
  * equilibrium r_i = f_eq_i(rho = 1, u = (U, 0)) of Eq. 3. */
 #define LBM_F32 0      /* float offsets, float arithmetic */
-#define LBM_F16_OFS 1  /* IEEE half offsets, float arithmetic */
+#define LBM_F16_OFS 1  /* IEEE half holding 4096 x the offset (exact power-of-two scale that keeps
+                          small offsets out of the binary16 subnormals), float arithmetic */
 #define LBM_BF16_OFS 2 /* bfloat16 offsets, float arithmetic */
 #define LBM_F64 3      /* double offsets, double arithmetic */
 

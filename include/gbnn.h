@@ -74,18 +74,23 @@ int gbnn_adam(float *param, const float *grad, float *m, float *v, void *param_b
               float beta1, float beta2, float eps, int t, void *stream);
 
 /* Network input of one sample, [H][W][8] bfloat16: solid flag, Re feature,
- * sin(phase), cos(phase), x/W, y/H, 0, 0.  solid: DEVICE uint8 [H][W]. */
-int gbnn_encode_input(const uint8_t *solid, float re_feature, float phase, int H, int W, void *x, void *stream);
+ * sin(phase), cos(phase), x/W, y/H, cos(k (x - x0) - phase),
+ * sin(k (x - x0) - phase) with k = wave_k (radians per node) and
+ * x0 = wave_x0 (a travelling-wave basis for the wake).  solid: DEVICE uint8
+ * [H][W]. */
+int gbnn_encode_input(const uint8_t *solid, float re_feature, float phase, float wave_k, float wave_x0, int H, int W,
+                      void *x, void *stream);
 
-/* Training target [P][3] = ((rho - 1)/rho_scale, u/U - 1, v/U) from DEVICE float
- * fields, and per-pixel loss weight (1 on fluid, 0 on solid; may be NULL). */
+/* Training target [P][3] = ((rho - 1)/rho_scale, (u - U)/vel_scale,
+ * v/vel_scale) from DEVICE float fields, and per-pixel loss weight (1 on
+ * fluid, 0 on solid; may be NULL). */
 int gbnn_encode_target(const float *rho, const float *u, const float *v, const uint8_t *solid, long long P, float U,
-                       float rho_scale, float *target, float *weight, void *stream);
+                       float vel_scale, float rho_scale, float *target, float *weight, void *stream);
 
 /* Inverse map of a network output (bfloat16, channels 0..2) to DEVICE float
  * fields; solid nodes get rho = 1, u = v = 0. */
-int gbnn_decode_output(const void *out, int out_cstride, const uint8_t *solid, long long P, float U, float rho_scale,
-                       float *rho, float *u, float *v, void *stream);
+int gbnn_decode_output(const void *out, int out_cstride, const uint8_t *solid, long long P, float U, float vel_scale,
+                       float rho_scale, float *rho, float *u, float *v, void *stream);
 
 /* cudaMemsetAsync(ptr, 0, bytes) on stream. */
 int gbnn_fill_zero(void *ptr, size_t bytes, void *stream);

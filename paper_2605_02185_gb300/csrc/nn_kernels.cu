@@ -460,47 +460,52 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
   }
 }
 
-// network input of one sample: [solid, Re feature, sin(phase), cos(phase), x/W, y/H, 0, 0]
-__global__ void encode_input_kernel(const uint8_t *__restrict__ solid, float re_feature, float s, float c, int H,
-                                    int W, bf16 *__restrict__ x) {
+// network input of one sample: [solid, Re feature, sin(phase), cos(phase),
+// x/W, y/H, cos(k (x - x0) - phase), sin(k (x - x0) - phase)]; the last two
+// are a travelling-wave basis (wavenumber k per node) for the wake
+__global__ void encode_input_kernel(const uint8_t *__restrict__ solid, float re_feature, float phase, float k,
+                                    float x0, int H, int W, bf16 *__restrict__ x) {
   const long long n = (long long)H * W;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int w = (int)(i % W), h = (int)(i / W);
     __align__(16) bf16 v[8];
+    const float arg = k * ((float)w - x0) - phase;
     v[0] = __float2bfloat16_rn(solid[i] ? 1.f : 0.f);
     v[1] = __float2bfloat16_rn(re_feature);
-    v[2] = __float2bfloat16_rn(s);
-    v[3] = __float2bfloat16_rn(c);
+    v[2] = __float2bfloat16_rn(sinf(phase));
+    v[3] = __float2bfloat16_rn(cosf(phase));
     v[4] = __float2bfloat16_rn((float)w / (float)W);
     v[5] = __float2bfloat16_rn((float)h / (float)H);
-    v[6] = v[7] = __float2bfloat16_rn(0.f);
+    v[6] = __float2bfloat16_rn(cosf(arg));
+    v[7] = __float2bfloat16_rn(sinf(arg));
     *reinterpret_cast<uint4 *>(x + i * 8) = *reinterpret_cast<const uint4 *>(v);
   }
 }
 
-// training target [P][3] = ((rho - 1) / rho_scale, u / U - 1, v / U), weight = fluid;
-// the velocity is taken relative to the free stream so that the network's
-// bfloat16 output resolves the deviations, not the mean flow
+// training target [P][3] = ((rho - 1) / rho_scale, (u - U) / vel_scale,
+// v / vel_scale), weight = fluid; the velocity is taken relative to the free
+// stream so that the network's bfloat16 output resolves the deviations
 __global__ void encode_target_kernel(const float *__restrict__ rho, const float *__restrict__ u,
                                      const float *__restrict__ v, const uint8_t *__restrict__ solid, long long P,
-                                     float U, float rho_scale, float *__restrict__ target, float *__restrict__ weight) {
+                                     float U, float vel_scale, float rho_scale, float *__restrict__ target,
+                                     float *__restrict__ weight) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
     target[3 * i] = (rho[i] - 1.f) / rho_scale;
-    target[3 * i + 1] = u[i] / U - 1.f;
-    target[3 * i + 2] = v[i] / U;
+    target[3 * i + 1] = (u[i] - U) / vel_scale;
+    target[3 * i + 2] = v[i] / vel_scale;
     if (weight) weight[i] = solid[i] ? 0.f : 1.f;
   }
 }
 
 // prediction -> fields (inverse of the target map); solid nodes rest at rho = 1
 __global__ void decode_output_kernel(const bf16 *__restrict__ out, int os, const uint8_t *__restrict__ solid,
-                                     long long P, float U, float rho_scale, float *__restrict__ rho,
+                                     long long P, float U, float vel_scale, float rho_scale, float *__restrict__ rho,
                                      float *__restrict__ u, float *__restrict__ v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
     const bool s = solid[i] != 0;
     rho[i] = s ? 1.f : 1.f + rho_scale * __bfloat162float(out[i * os]);
-    u[i] = s ? 0.f : U * (1.f + __bfloat162float(out[i * os + 1]));
-    v[i] = s ? 0.f : U * __bfloat162float(out[i * os + 2]);
+    u[i] = s ? 0.f : U + vel_scale * __bfloat162float(out[i * os + 1]);
+    v[i] = s ? 0.f : vel_scale * __bfloat162float(out[i * os + 2]);
   }
 }
 
@@ -627,26 +632,27 @@ int gbnn_mse(const void *pred, int pred_cstride, const float *target, const floa
   return err(cudaGetLastError());
 }
 
-int gbnn_encode_input(const uint8_t *solid, float re_feature, float phase, int H, int W, void *x, void *stream) {
+int gbnn_encode_input(const uint8_t *solid, float re_feature, float phase, float wave_k, float wave_x0, int H, int W,
+                      void *x, void *stream) {
   if (!solid || !x || H <= 0 || W <= 0 || ((uintptr_t)x % 16)) return -1;
   encode_input_kernel<<<grid_for((long long)H * W), 256, 0, (cudaStream_t)stream>>>(
-      solid, re_feature, sinf(phase), cosf(phase), H, W, (bf16 *)x);
+      solid, re_feature, phase, wave_k, wave_x0, H, W, (bf16 *)x);
   return err(cudaGetLastError());
 }
 
 int gbnn_encode_target(const float *rho, const float *u, const float *v, const uint8_t *solid, long long P, float U,
-                       float rho_scale, float *target, float *weight, void *stream) {
-  if (!rho || !u || !v || !solid || !target || P <= 0 || !(U > 0.f) || !(rho_scale > 0.f)) return -1;
-  encode_target_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>(rho, u, v, solid, P, U, rho_scale, target,
-                                                                       weight);
+                       float vel_scale, float rho_scale, float *target, float *weight, void *stream) {
+  if (!rho || !u || !v || !solid || !target || P <= 0 || !(vel_scale > 0.f) || !(rho_scale > 0.f)) return -1;
+  encode_target_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>(rho, u, v, solid, P, U, vel_scale, rho_scale,
+                                                                       target, weight);
   return err(cudaGetLastError());
 }
 
-int gbnn_decode_output(const void *out, int out_cstride, const uint8_t *solid, long long P, float U, float rho_scale,
-                       float *rho, float *u, float *v, void *stream) {
+int gbnn_decode_output(const void *out, int out_cstride, const uint8_t *solid, long long P, float U, float vel_scale,
+                       float rho_scale, float *rho, float *u, float *v, void *stream) {
   if (!out || !solid || !rho || !u || !v || P <= 0 || out_cstride < 3) return -1;
   decode_output_kernel<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>((const bf16 *)out, out_cstride, solid, P, U,
-                                                                       rho_scale, rho, u, v);
+                                                                       vel_scale, rho_scale, rho, u, v);
   return err(cudaGetLastError());
 }
 

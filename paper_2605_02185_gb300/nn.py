@@ -34,9 +34,9 @@ def _lib():
             "gbnn_upsample2_bwd": [vp, i, vp, i, i, i, i, i, vp],
             "gbnn_mse": [vp, i, vp, vp, vp, i, ll, i, f, vp, vp],
             "gbnn_adam": [vp, vp, vp, vp, vp, ll, f, f, f, f, i, vp],
-            "gbnn_encode_input": [vp, f, f, i, i, vp, vp],
-            "gbnn_encode_target": [vp, vp, vp, vp, ll, f, f, vp, vp, vp],
-            "gbnn_decode_output": [vp, i, vp, ll, f, f, vp, vp, vp, vp],
+            "gbnn_encode_input": [vp, f, f, f, f, i, i, vp, vp],
+            "gbnn_encode_target": [vp, vp, vp, vp, ll, f, f, f, vp, vp, vp],
+            "gbnn_decode_output": [vp, i, vp, ll, f, f, f, vp, vp, vp, vp],
             "gbnn_fill_zero": [vp, sz, vp],
         }
         for name, args in sig.items():
@@ -111,19 +111,19 @@ def adam(param, grad, m, v, param_bf16, n, lr, t, beta1=0.9, beta2=0.999, eps=1e
                          float(beta2), float(eps), int(t), _s(stream)), "gbnn_adam")
 
 
-def encode_input(solid, re_feature, phase, H, W, x, stream=None):
-    _ck(_lib().gbnn_encode_input(_p(solid), float(re_feature), float(phase), H, W, _p(x), _s(stream)),
-        "gbnn_encode_input")
+def encode_input(solid, re_feature, phase, H, W, x, stream=None, wave_k=0.0, wave_x0=0.0):
+    _ck(_lib().gbnn_encode_input(_p(solid), float(re_feature), float(phase), float(wave_k), float(wave_x0), H, W, _p(x),
+                                 _s(stream)), "gbnn_encode_input")
 
 
-def encode_target(rho, u, v, solid, P, U, rho_scale, target, weight, stream=None):
-    _ck(_lib().gbnn_encode_target(_p(rho), _p(u), _p(v), _p(solid), int(P), float(U), float(rho_scale), _p(target),
-                                  _p(weight), _s(stream)), "gbnn_encode_target")
+def encode_target(rho, u, v, solid, P, U, vel_scale, rho_scale, target, weight, stream=None):
+    _ck(_lib().gbnn_encode_target(_p(rho), _p(u), _p(v), _p(solid), int(P), float(U), float(vel_scale),
+                                  float(rho_scale), _p(target), _p(weight), _s(stream)), "gbnn_encode_target")
 
 
-def decode_output(out, os_, solid, P, U, rho_scale, rho, u, v, stream=None):
-    _ck(_lib().gbnn_decode_output(_p(out), os_, _p(solid), int(P), float(U), float(rho_scale), _p(rho), _p(u), _p(v),
-                                  _s(stream)), "gbnn_decode_output")
+def decode_output(out, os_, solid, P, U, vel_scale, rho_scale, rho, u, v, stream=None):
+    _ck(_lib().gbnn_decode_output(_p(out), os_, _p(solid), int(P), float(U), float(vel_scale), float(rho_scale),
+                                  _p(rho), _p(u), _p(v), _s(stream)), "gbnn_decode_output")
 
 
 def fill_zero(t, stream=None):
@@ -174,7 +174,7 @@ class WarmStartNet:
     IN_C = 8
     OUT_C = 8
 
-    def __init__(self, N, H, W, device, seed=0):
+    def __init__(self, N, H, W, device, seed=0, zero_head=False):
         import torch
         assert H % 8 == 0 and W % 8 == 0
         self.N, self.H, self.W = N, H, W
@@ -189,7 +189,7 @@ class WarmStartNet:
             "d3a": Conv(C[3] + C[2], C[2], rng, device), "d3b": Conv(C[2], C[2], rng, device),
             "d2a": Conv(C[2] + C[1], C[1], rng, device), "d2b": Conv(C[1], C[1], rng, device),
             "d1a": Conv(C[1] + C[0], C[0], rng, device), "d1b": Conv(C[0], C[0], rng, device),
-            "head": Conv(C[0], self.OUT_C, rng, device, relu=False),
+            "head": Conv(C[0], self.OUT_C, rng, device, relu=False, zero=zero_head),
         }
         self.t = 0
         bf = torch.bfloat16

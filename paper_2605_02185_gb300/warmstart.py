@@ -40,8 +40,8 @@ class Config:
     replay: int = 1024        # snapshots held in the replay buffer (device memory)
     iters: int = 0            # training iterations; 0: snapshots // batch
     batch: int = 4
-    lr: float = 1e-3
-    lr_final: float = 1e-4
+    lr: float = 3e-4
+    lr_final: float = 2e-5
     stride: int = 37          # solver steps between snapshot rounds
     chunk: int = 1000         # steps between periodicity checks
     spinup_max: int = 400_000
@@ -51,11 +51,18 @@ class Config:
     eval_seed: int = 11
     perturb: float = 1e-3     # cold start: seeded +-perturb U velocity noise
     train_perturb: float = 0.1  # training cases start from a larger kick (earlier shedding onset)
-    rho_factor: float = 8.0   # density target (rho - 1) / (rho_factor U^2)
+    rho_factor: float = 1.0   # density target (rho - 1) / (rho_factor U^2)
+    vel_factor: float = 0.2   # velocity targets (u - U, v) / (vel_factor U)
+    warmup: int = 300         # training iterations of linear learning-rate warm-up
+    wave_len: float = 5.0     # wavelength (in D) of the travelling-wave input basis; 0: none
 
     @property
     def rho_scale(self) -> float:
         return self.rho_factor * self.U * self.U
+
+    @property
+    def vel_scale(self) -> float:
+        return self.vel_factor * self.U
 
     @property
     def train_iters(self) -> int:
@@ -69,6 +76,13 @@ def re_values(n: int, seed: int, lo: float, hi: float) -> np.ndarray:
 
 def re_feature(Re: float, cfg: Config) -> float:
     return 2.0 * (math.log(Re) - math.log(cfg.re_lo)) / (math.log(cfg.re_hi) - math.log(cfg.re_lo)) - 1.0
+
+
+def net_input(cfg: Config, solid, Re_feature: float, phase: float, H: int, Wd: int, x, stream):
+    """Network input of one sample (mask, Re, phase, coordinates and a wake
+    travelling-wave basis cos/sin(2 pi (x - 10 D) / (wave_len D) - phase))."""
+    k = 2 * math.pi / (cfg.wave_len * cfg.D) if cfg.wave_len > 0 else 0.0
+    nn.encode_input(solid, Re_feature, phase, H, Wd, x, stream, wave_k=k, wave_x0=10.0 * cfg.D)
 
 
 def case_for(Re: float, cfg: Config, seed: int, perturb: float | None = None) -> W.Workload:
@@ -152,7 +166,7 @@ class SnapshotSource:
 
 class Replay:
     """Ring of labelled training snapshots in device memory: targets
-    ((rho - 1) / rho_scale, u / U - 1, v / U) per node and (Re feature, phase)."""
+    ((rho - 1) / rho_scale, (u - U) / vel_scale, v / vel_scale) per node and (Re feature, phase)."""
 
     def __init__(self, cfg: Config, src: SnapshotSource, device):
         import torch
@@ -178,8 +192,8 @@ class Replay:
         for c in cases:
             k = self.made % self.cap
             lbm.lbm_fields_device(src.batch.case(c), *(t.data_ptr() for t in self.fr))
-            nn.encode_target(self.fr[0], self.fr[1], self.fr[2], src.solid, self.P, cfg.U, cfg.rho_scale, self.T[k],
-                             self.weight, stream)
+            nn.encode_target(self.fr[0], self.fr[1], self.fr[2], src.solid, self.P, cfg.U, cfg.vel_scale,
+                             cfg.rho_scale, self.T[k], self.weight, stream)
             self.ref[k] = re_feature(float(src.res[c]), cfg)
             self.phase[k] = src.phase(c)
             self.made += 1
@@ -205,7 +219,7 @@ def train(cfg: Config, device=None, log=print):
     P1 = H * Wd
     rng = np.random.default_rng(cfg.seed)
     with torch.cuda.stream(stream):
-        net = nn.WarmStartNet(B, H, Wd, device, seed=cfg.seed)
+        net = nn.WarmStartNet(B, H, Wd, device, seed=cfg.seed, zero_head=True)
         target = torch.empty((B * P1, 3), dtype=torch.float32, device=device)
         weight = torch.empty(B * P1, dtype=torch.float32, device=device)
         rep = Replay(cfg, src, device)
@@ -226,13 +240,15 @@ def train(cfg: Config, device=None, log=print):
                 done_rounds += 1
             idx = rng.integers(0, rep.filled, B)
             for j, k in enumerate(idx):
-                nn.encode_input(src.solid, float(rep.ref[k]), float(rep.phase[k]), H, Wd, net.x0[j], stream)
+                net_input(cfg, src.solid, float(rep.ref[k]), float(rep.phase[k]), H, Wd, net.x0[j], stream)
                 target[j * P1:(j + 1) * P1].copy_(rep.T[k])
             net.forward(stream)
             loss = net.loss_and_grad(target, weight, stream)
             net.backward(stream)
             frac = it / max(iters - 1, 1)
             lr = cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1 + math.cos(math.pi * frac))
+            if it < cfg.warmup:
+                lr *= (it + 1) / cfg.warmup
             net.adam_step(lr, stream)
             if it % 50 == 0 or it == iters - 1:
                 stream.synchronize()
@@ -294,9 +310,10 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        nn.encode_input(solid, re_feature(Re, cfg), 0.0, wl.ny, wl.nx, pred.x0[0], stream)
+        net_input(cfg, solid, re_feature(Re, cfg), 0.0, wl.ny, wl.nx, pred.x0[0], stream)
         pred.forward(stream)
-        nn.decode_output(pred.out, pred.OUT_C, solid, wl.nx * wl.ny, cfg.U, cfg.rho_scale, fr[0], fr[1], fr[2], stream)
+        nn.decode_output(pred.out, pred.OUT_C, solid, wl.nx * wl.ny, cfg.U, cfg.vel_scale, cfg.rho_scale, fr[0], fr[1],
+                         fr[2], stream)
     stream.synchronize()
     t_inf = time.perf_counter() - t0
     lbm.lbm_init_fields_device(lat.h, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr(), True)

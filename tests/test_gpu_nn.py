@@ -275,10 +275,10 @@ def test_network_trains_on_a_fixed_target():
 
 
 def test_encoders_and_decoder():
-    """Network input channels; targets ((rho - 1)/s, u/U - 1, v/U) with the
+    """Network input channels; targets ((rho - 1)/s, (u - U)/q, v/q) with the
     fluid weight; the decoder inverts the target map of a bfloat16 output."""
     rng = np.random.default_rng(17)
-    H, W, U, s = 7, 12, 0.05, 8 * 0.05 ** 2
+    H, W, U, s, q = 7, 12, 0.05, 8 * 0.05 ** 2, 0.01
     P = H * W
     solid = np.zeros((H, W), np.uint8)
     solid[3, 4:7] = 1
@@ -289,23 +289,23 @@ def test_encoders_and_decoder():
     tr, tu, tv = (torch.from_numpy(a).to(DEV) for a in (rho, u, v))
     target = torch.empty((P, 3), dtype=torch.float32, device=DEV)
     weight = torch.empty(P, dtype=torch.float32, device=DEV)
-    nn.encode_target(tr, tu, tv, t_solid, P, U, s, target, weight)
-    want = np.stack([(rho - np.float32(1)) / np.float32(s), u / np.float32(U) - np.float32(1), v / np.float32(U)],
+    nn.encode_target(tr, tu, tv, t_solid, P, U, q, s, target, weight)
+    want = np.stack([(rho - np.float32(1)) / np.float32(s), (u - np.float32(U)) / np.float32(q), v / np.float32(q)],
                     -1).reshape(P, 3)
     np.testing.assert_allclose(target.cpu().numpy(), want, rtol=1e-6, atol=1e-6)
     assert np.array_equal(weight.cpu().numpy(), 1.0 - solid.reshape(-1))
     out = torch.zeros((P, 8), dtype=torch.bfloat16, device=DEV)
     out[:, :3] = target.to(torch.bfloat16)
     r2, u2, v2 = (torch.empty((H, W), dtype=torch.float32, device=DEV) for _ in range(3))
-    nn.decode_output(out, 8, t_solid, P, U, s, r2, u2, v2)
+    nn.decode_output(out, 8, t_solid, P, U, q, s, r2, u2, v2)
     o = out[:, :3].float().cpu().numpy().reshape(H, W, 3)
     fl = solid == 0
     np.testing.assert_allclose(r2.cpu().numpy()[fl], (1 + s * o[..., 0])[fl], rtol=1e-6)
-    np.testing.assert_allclose(u2.cpu().numpy()[fl], (U * (1 + o[..., 1]))[fl], rtol=1e-6)
-    np.testing.assert_allclose(v2.cpu().numpy()[fl], (U * o[..., 2])[fl], rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(u2.cpu().numpy()[fl], (U + q * o[..., 1])[fl], rtol=1e-6)
+    np.testing.assert_allclose(v2.cpu().numpy()[fl], (q * o[..., 2])[fl], rtol=1e-6, atol=1e-9)
     assert np.all(r2.cpu().numpy()[~fl] == 1) and np.all(u2.cpu().numpy()[~fl] == 0)
     x = torch.empty((H, W, 8), dtype=torch.bfloat16, device=DEV)
-    nn.encode_input(t_solid, 0.25, 1.0, H, W, x)
+    nn.encode_input(t_solid, 0.25, 1.0, H, W, x, wave_k=0.3, wave_x0=2.0)
     xs = x.float().cpu().numpy()
     assert np.array_equal(xs[..., 0], solid.astype(np.float32))
     np.testing.assert_allclose(xs[..., 1], 0.25)
@@ -313,3 +313,6 @@ def test_encoders_and_decoder():
     np.testing.assert_allclose(xs[..., 3], np.cos(1.0), rtol=4e-3)
     np.testing.assert_allclose(xs[..., 4], np.arange(W)[None, :] / W * np.ones((H, 1)), rtol=4e-3, atol=1e-6)
     np.testing.assert_allclose(xs[..., 5], np.arange(H)[:, None] / H * np.ones((1, W)), rtol=4e-3, atol=1e-6)
+    arg = 0.3 * (np.arange(W)[None, :] - 2.0) - 1.0 + np.zeros((H, 1))
+    np.testing.assert_allclose(xs[..., 6], np.cos(arg), atol=4e-3)
+    np.testing.assert_allclose(xs[..., 7], np.sin(arg), atol=4e-3)

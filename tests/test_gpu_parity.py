@@ -66,6 +66,8 @@ def gpu_run(wl, steps, **kw):
 def offsets_to_f(pops, U, storage=lbm.LBM_F32):
     if storage == lbm.LBM_BF16_OFS:
         g = (pops.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    elif storage == lbm.LBM_F16_OFS:
+        g = pops.astype(np.float64) / 4096.0  # IEEE half holds 2^12 x the offset
     else:
         g = pops.astype(np.float64)
     return g + reference_pops(U)[:, None, None]
