@@ -1,6 +1,7 @@
-"""Learned warm start end to end on a reduced problem (D = 20, 800 x 400):
-snapshots from the batched solver, training with the library's tensor-core
-kernels, warm vs cold start to periodic shedding on held-out Re."""
+"""Learned warm start end to end on a reduced problem (D = 20, 800 x 400,
+Re in [60, 85], where the cold start reaches a clean limit cycle): snapshots
+from the batched solver, training with the library's tensor-core kernels,
+warm vs cold start to periodic shedding on held-out Re."""
 import numpy as np
 import pytest
 
@@ -14,12 +15,12 @@ from paper_2605_02185_gb300 import warmstart as WS  # noqa: E402
 
 
 def test_warm_start_gains_over_cold_start():
-    cfg = WS.Config(D=20, train_cases=8, snapshots=2000, batch=4, lr=3e-4, lr_final=3e-5, stride=23,
-                    spinup_max=300_000, eval_max=300_000, chunk=500)
+    cfg = WS.Config(D=20, re_hi=85.0, train_cases=12, snapshots=9000, replay=512, iters=3000, batch=4,
+                    stride=37, spinup_max=300_000, eval_max=200_000, chunk=500)
     dev = torch.device("cuda")
     net, info = WS.train(cfg, dev, log=lambda m: None)
     first, last = info["losses"][0][1], info["losses"][-1][1]
-    assert last < 0.3 * first, info["losses"]
+    assert last < 0.1 * first, info["losses"]
     rows, summary = WS.evaluate(net, cfg, n_eval=2, device=dev, log=lambda m: None)
     for r in rows:
         assert r["cold"]["steps"] is not None  # the judge itself reached periodic shedding
