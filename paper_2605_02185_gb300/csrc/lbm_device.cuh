@@ -352,6 +352,25 @@ __device__ __forceinline__ Coef<L> make_coef(const StepParams &p) {
   return k;
 }
 
+// The one-node float constants in both lanes of a pair (the same values
+// make_coef<LF2> gives).
+__device__ __forceinline__ LF2 widen(LF a) { return {make_float2(a.v, a.v)}; }
+__device__ __forceinline__ Coef<LF2> widen(const Coef<LF> &c) {
+  Coef<LF2> k;
+  k.U = widen(c.U);
+  k.nUU = widen(c.nUU);
+  k.om = widen(c.om);
+  k.omc = widen(c.omc);
+  k.w36 = widen(c.w36);
+  k.w9 = widen(c.w9);
+  k.w2 = widen(c.w2);
+  k.w4 = widen(c.w4);
+  k.se36 = widen(c.se36);
+  k.seps36 = widen(c.seps36);
+  k.sq12 = widen(c.sq12);
+  return k;
+}
+
 // BGK collision (Eq. 2) towards Eq. 3 with the moments of Eq. 4, on h.
 // delta_rho = sum h, j = (U, 0) + dj with dj = sum h c, and
 //   h_eq_k = w_k [delta_rho + 3 c.dj + (9/2 ((c.dj)(c.j + c.U) - delta_rho (c.U)^2)

@@ -45,17 +45,33 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
 }
 
 // Collision of one node held in C values (Eq. 2 or Eq. 6); false when the
-// node's speed left the stable range.
+// node's speed left the stable range.  For the 16-bit storage forms, whose
+// plain spans are updated two nodes at a time with packed instructions, a
+// single node runs the same packed instructions with itself in both lanes:
+// inside the step kernels the packed and the one-lane instruction sequences
+// were seen to disagree in the last bit on rare nodes, and running one form
+// keeps every kernel and shape bit-identical.
 template <int MRT, class S>
 __device__ __forceinline__ bool collide_node(typename Store<S>::C (&h)[9], const Coef<Lane<S>> &cf) {
   using L = Lane<S>;
-  L v[9];
+  if constexpr (sizeof(S) == 2) {
+    const Coef<LF2> c2 = widen(cf);
+    LF2 v[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) v[k] = L{h[k]};
-  const bool ok = speed_ok(collide_model<MRT, L>(v, cf));
+    for (int k = 0; k < 9; ++k) v[k] = LF2{make_float2(h[k], h[k])};
+    const bool ok = speed_ok(collide_model<MRT, LF2>(v, c2));
 #pragma unroll
-  for (int k = 0; k < 9; ++k) h[k] = v[k].v;
-  return ok;
+    for (int k = 0; k < 9; ++k) h[k] = v[k].v.x;
+    return ok;
+  } else {
+    L v[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) v[k] = L{h[k]};
+    const bool ok = speed_ok(collide_model<MRT, L>(v, cf));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) h[k] = v[k].v;
+    return ok;
+  }
 }
 
 // One node, general form: pull (with bounce-back and placeholders), boundary
