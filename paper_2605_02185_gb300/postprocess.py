@@ -76,6 +76,18 @@ def periodic_index(cl, amp_min: float = 0.05, tol: float = 0.005, consecutive: i
     return None
 
 
+def limit_cycle(cl, periods: int = 6, tol: float = 0.01, amp_min: float = 0.05) -> bool:
+    """True when the last `periods` complete lift periods all have amplitude
+    >= amp_min and spread by less than tol (relative to their mean): a clean
+    limit cycle, as opposed to a modulated or chaotic lift that passes the
+    period-to-period test by chance."""
+    a = period_amplitudes(cl)
+    if len(a) < periods:
+        return False
+    a = a[-periods:]
+    return bool(a.min() >= amp_min and (a.max() - a.min()) < tol * a.mean())
+
+
 def statistics(cd, cl, D: float, U: float, periods: int | None = None) -> dict:
     """Mean Cd, Cl amplitude and Strouhal number over the window: the last
     `periods` complete lift periods (all of them if None)."""

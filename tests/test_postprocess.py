@@ -28,3 +28,14 @@ def test_periodicity_detector():
     # 0.5 % near n ~ 9.4k; two such periods later the detector fires
     assert 9000 < i < 12000
     assert PP.periodic_index(1e-3 * np.sin(2 * math.pi * n / T)) is None  # below the amplitude floor
+
+
+def test_limit_cycle_separates_clean_from_modulated_lift():
+    n = np.arange(60000)
+    T = 2500.0
+    clean = 0.3 * np.sin(2 * math.pi * n / T)
+    beat = 0.3 * (1 + 0.03 * np.sin(2 * math.pi * n / (6.3 * T))) * np.sin(2 * math.pi * n / T)
+    assert PP.limit_cycle(clean)
+    assert not PP.limit_cycle(beat)
+    assert not PP.limit_cycle(clean[:int(3 * T)])        # too few periods
+    assert not PP.limit_cycle(0.01 * clean)              # below the amplitude floor
