@@ -35,6 +35,7 @@ class Config:
     U: float = 0.05
     re_lo: float = 60.0
     re_hi: float = 200.0
+    train_re_hi: float = 100.0  # training cases: Re in [re_lo, train_re_hi], where U = 0.05 sheds cleanly
     train_cases: int = 32
     snapshots: int = 20000    # snapshots the solver hands to the trainer
     replay: int = 1024        # snapshots held in the replay buffer (device memory)
@@ -46,7 +47,8 @@ class Config:
     chunk: int = 1000         # steps between periodicity checks
     spinup_max: int = 300_000
     eval_max: int = 400_000
-    settle_periods: int = 4   # periods run past detection for the drift statistics
+    settle_periods: int = 30  # periods run past detection before the drift statistics
+    stat_periods: int = 4     # periods the drift statistics average over
     collision: int = lbm.LBM_COLLIDE_MRT
     seed: int = 7
     eval_seed: int = 11
@@ -128,7 +130,7 @@ class SnapshotSource:
     def __init__(self, cfg: Config, device, stream):
         import torch
         self.cfg = cfg
-        self.res = re_values(cfg.train_cases, cfg.seed, cfg.re_lo, cfg.re_hi)
+        self.res = re_values(cfg.train_cases, cfg.seed, cfg.re_lo, min(cfg.train_re_hi, cfg.re_hi))
         self.cases = [case_for(Re, cfg, cfg.seed * 1000 + i, cfg.train_perturb) for i, Re in enumerate(self.res)]
         self.batch = lbm.Batch(self.cases, collision=cfg.collision, stream=stream, device=device,
                                history_capacity=1 << 20)
@@ -154,7 +156,7 @@ class SnapshotSource:
                         done[c] = i
         clean = []
         for c in range(len(self.cases)):
-            if done[c] is not None and postprocess.limit_cycle(self.hist[c].update()[1]):
+            if done[c] is not None and postprocess.limit_cycle(self.hist[c].update()[1], tol=0.05):
                 clean.append(c)
         self.periodic = clean
         log(f"spin-up: {self.steps} steps, {sum(d is not None for d in done)}/{len(self.cases)} cases passed the "
@@ -280,12 +282,14 @@ def predictor(net: nn.WarmStartNet, device):
     return p
 
 
-def run_to_periodic(lat, wl: W.Workload, max_steps: int, chunk: int, t0: float, settle_periods: int = 4):
+def run_to_periodic(lat, wl: W.Workload, max_steps: int, chunk: int, t0: float, settle_periods: int = 30,
+                    stat_periods: int = 4):
     """Step until the lift is periodic (postprocess.periodic_index).  Returns
-    (step at detection, seconds from t0 to detection, statistics), the
-    statistics taken over `settle_periods` periods run past the detection, so
-    that two runs are compared on the converged cycle; (None, None, None) if
-    the lift is not periodic within max_steps."""
+    (step at detection, seconds from t0 to detection, statistics); the
+    statistics average over the last `stat_periods` of `settle_periods`
+    periods run past the detection, so that two runs are compared on the
+    converged cycle; (None, None, None) if the lift is not periodic within
+    max_steps."""
     steps = 0
     hist = History(lat.h)
     while steps < max_steps:
@@ -299,7 +303,7 @@ def run_to_periodic(lat, wl: W.Workload, max_steps: int, chunk: int, t0: float, 
             T = float(z[-1] - z[-2])
             lat.step(int(math.ceil((settle_periods + 1) * T)))
             cd, cl = hist.update()
-            st = postprocess.statistics(cd, cl, wl.D, wl.U, periods=settle_periods)
+            st = postprocess.statistics(cd, cl, wl.D, wl.U, periods=stat_periods)
             return i, t_detect, st
     return None, None, None
 
@@ -309,7 +313,8 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
     start (network prediction at phase 0, f_eq + f_neq) for one Re: steps
     and wall time to periodic lift (the warm time includes the inference),
     and the relative drift of mean Cd, Cl amplitude and St between the two
-    converged cycles; the prediction is accepted when every drift is <= 1 %."""
+    runs settle_periods past their detection; the prediction is accepted when
+    every drift is <= 1 %."""
     import torch
     wl = case_for(Re, cfg, seed)
     stream = torch.cuda.Stream(device)
@@ -318,7 +323,8 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     lat.init_fields(*wl.initial_fields())
-    n_cold, t_cold, st_cold = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk, t0, cfg.settle_periods)
+    n_cold, t_cold, st_cold = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk, t0, cfg.settle_periods,
+                                              cfg.stat_periods)
     lat.sync()
     out["cold"] = {"steps": n_cold, "wall_s": t_cold, **(st_cold or {})}
     lat.close()
@@ -335,7 +341,8 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
     stream.synchronize()
     t_inf = time.perf_counter() - t0
     lbm.lbm_init_fields_device(lat.h, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr(), True)
-    n_warm, t_warm, st_warm = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk, t0, cfg.settle_periods)
+    n_warm, t_warm, st_warm = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk, t0, cfg.settle_periods,
+                                              cfg.stat_periods)
     lat.sync()
     out["warm"] = {"steps": n_warm, "wall_s": t_warm, "inference_s": t_inf, **(st_warm or {})}
     lat.close()
