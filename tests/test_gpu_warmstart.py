@@ -25,6 +25,7 @@ def test_warm_start_gains_over_cold_start():
     for r in rows:
         assert r["cold"]["steps"] is not None  # the judge itself reached periodic shedding
         assert r["warm"]["steps"] is not None
+        # the same converged cycle: mean drag and Strouhal number within 1 %
+        assert r["drift"]["cd_mean"] <= 0.01 and r["drift"]["st"] <= 0.01, r
     # the gain: fewer steps to periodic shedding from the prediction
-    assert summary["accepted"] >= 1, rows
-    assert summary["median_step_speedup"] > 1.0, rows
+    assert np.median([r["step_speedup"] for r in rows]) > 1.0, rows
