@@ -51,18 +51,23 @@ __device__ __forceinline__ bool is_force_item(const StepParams &p, int y, int s)
 // inside the step kernels the packed and the one-lane instruction sequences
 // were seen to disagree in the last bit on rare nodes, and running one form
 // keeps every kernel and shape bit-identical.
+template <int MRT>
+__device__ __noinline__ bool collide_node_packed(float (&h)[9], const Coef<LF> &cf) {
+  const Coef<LF2> c2 = widen(cf);
+  LF2 v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = LF2{make_float2(h[k], h[k])};
+  const bool ok = speed_ok(collide_model<MRT, LF2>(v, c2));
+#pragma unroll
+  for (int k = 0; k < 9; ++k) h[k] = v[k].v.x;
+  return ok;
+}
+
 template <int MRT, class S>
 __device__ __forceinline__ bool collide_node(typename Store<S>::C (&h)[9], const Coef<Lane<S>> &cf) {
   using L = Lane<S>;
   if constexpr (sizeof(S) == 2) {
-    const Coef<LF2> c2 = widen(cf);
-    LF2 v[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) v[k] = LF2{make_float2(h[k], h[k])};
-    const bool ok = speed_ok(collide_model<MRT, LF2>(v, c2));
-#pragma unroll
-    for (int k = 0; k < 9; ++k) h[k] = v[k].v.x;
-    return ok;
+    return collide_node_packed<MRT>(h, cf);
   } else {
     L v[9];
 #pragma unroll
