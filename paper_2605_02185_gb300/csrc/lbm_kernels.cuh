@@ -134,6 +134,48 @@ __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams
   store_node<S>(B, p, x, y, h);
 }
 
+// Two adjacent nodes x, x + 1 of a span that needs the general form (pull
+// with bounce-back and placeholders, boundary rules, links): each node is
+// pulled on its own, the pair collides in the packed form the plain spans
+// use, so a node gets the same bits whichever span it falls in.
+template <int MRT, class S, class Fetch>
+__device__ __forceinline__ void update_node_pair(const S *__restrict__ A, S *__restrict__ B, const StepParams &p,
+                                                 int x, int y, const Coef<LF2> &cf2, Fetch fetch, double &fx,
+                                                 double &fy, bool &bad) {
+  float h[2][9];
+  uint32_t lm[2];
+  int xe[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int xn = x + e;
+    xe[e] = (xn == p.nx - 1) ? p.nx - 2 : xn;  // Eq. 13: outlet = column nx-2
+    lm[e] = xn < p.nx ? link_mask(p, xe[e], y) : LM_SOLID;
+    if (lm[e] & LM_SOLID) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) h[e][k] = 0.f;
+    } else {
+      pull<S>(A, p, xe[e], y, lm[e], fetch, h[e]);
+      boundaries<float>(h[e], xe[e], y, p);
+    }
+  }
+  LF2 v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = LF2{make_float2(h[0][k], h[1][k])};
+  const LF2 uu = collide_model<MRT, LF2>(v, cf2);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int xn = x + e;
+    if (xn >= p.nx) continue;
+    if (!(lm[e] & LM_SOLID)) {
+      bad |= !((e ? uu.v.y : uu.v.x) <= 0.09f);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) h[e][k] = e ? v[k].v.y : v[k].v.x;
+      if ((lm[e] & LM_LINKS) && xn == xe[e]) link_force<float>(h[e], lm[e], fx, fy);
+    }
+    store_node<S>(B, p, xn, y, h[e]);
+  }
+}
+
 // Two adjacent interior nodes (x even) of a plain span, from a staged row
 // tile (tile[k * seg + x'] = h*_k at column x' of row y - c_ky): the
 // x-aligned planes are read as one pair, the x-shifted ones per node; the
@@ -299,13 +341,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
         const int xw = x0 + (c * NC + (ctid & ~31)) * PX;
         if constexpr (PX == 2) {
           const int x = xw + 2 * lane;
-          if (plain_span(p, xw, xw + 63, y)) {
+          if (plain_span(p, xw, xw + 63, y))
             update_pair<MRT, S>(B, p, x, y, cf2, tile, SEG, bad);
-          } else {
-#pragma unroll 1
-            for (int e = 0; e < 2; ++e)
-              if (x + e < p.nx) update_node<MRT, S>(A, B, p, x + e, y, cf, fetch, fx, fy, bad);
-          }
+          else if (x < p.nx)
+            update_node_pair<MRT, S>(A, B, p, x, y, cf2, fetch, fx, fy, bad);
         } else {
           const int x = xw + lane;
           if (plain_span(p, xw, xw + 31, y))
@@ -492,13 +531,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         const int xw = x0 + (cc * NC + (ctid & ~31)) * PX;
         if constexpr (PX == 2) {
           const int x = xw + 2 * lane;
-          if (plain_span(p, xw, xw + 63, y)) {
-            update_pair<MRT, S>(B, p, x, y, make_coef<LF2>(p), tile, SEG, bad);
-          } else {
-#pragma unroll 1
-            for (int e = 0; e < 2; ++e)
-              if (x + e < p.nx) update_node<MRT, S>(A, B, p, x + e, y, cf, fetch, fx, fy, bad);
-          }
+          const Coef<LF2> cf2 = widen(cf);
+          if (plain_span(p, xw, xw + 63, y))
+            update_pair<MRT, S>(B, p, x, y, cf2, tile, SEG, bad);
+          else if (x < p.nx)
+            update_node_pair<MRT, S>(A, B, p, x, y, cf2, fetch, fx, fy, bad);
         } else {
           const int x = xw + lane;
           if (plain_span(p, xw, xw + 31, y))
