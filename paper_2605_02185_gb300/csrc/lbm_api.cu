@@ -270,6 +270,7 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.s_e = o->s_e;
   p.s_eps = o->s_eps;
   p.s_q = o->s_q;
+  fill_coefs(p);
 
   int shape = default_shape(o->storage);
   int kernel = o->kernel;

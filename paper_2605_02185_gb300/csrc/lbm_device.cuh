@@ -124,7 +124,45 @@ struct StepParams {
   double fconst_x, fconst_y;    // sum over links of 2 r_i c_i (the reference part of Eq. 14)
   int mrt;                      // 0: BGK (Eq. 2); 1: MRT (Eq. 6)
   double s_e, s_eps, s_q;       // MRT rates of e, epsilon and q (the shear rate is omega)
+  // collision constants rounded once on the host (fill_coefs), in the order
+  // U, -U^2, omega, 1 - omega, omega/36, omega/9, omega/2, omega/4, s_e/36,
+  // s_eps/36, s_q/12: float for the float lanes, double for the double lane
+  float kf[11];
+  double kd[11];
 };
+
+// omega and 1 - omega rounded as a pair that is exact in T and sums to
+// exactly 1 (Sterbenz: x - y is exact for y/2 <= x <= 2y), so the BGK update
+// (1 - omega) h + omega h_eq carries mass and momentum over without a
+// systematic bias from rounding omega.
+template <class T>
+__host__ __device__ inline void relaxation_pair(double omega, T &om, T &omc) {
+  om = (T)omega;
+  if (om >= (T)0.5) {
+    omc = (T)1 - om;
+  } else {
+    omc = (T)(1.0 - omega);
+    om = (T)1 - omc;
+  }
+}
+
+// Fill StepParams::kf / kd from omega, U and the MRT rates (host side, once
+// per lattice; the kernels only load them).
+__host__ __device__ inline void fill_coefs(StepParams &p) {
+  float omf, omcf;
+  relaxation_pair<float>(p.omega, omf, omcf);
+  double omd, omcd;
+  relaxation_pair<double>(p.omega, omd, omcd);
+  const double of = omf, ocf = omcf;
+  const double vf[11] = {p.U, -p.U * p.U, of, ocf, of / 36.0, of / 9.0, 0.5 * of, 0.25 * of,
+                         p.s_e / 36.0, p.s_eps / 36.0, p.s_q / 12.0};
+  const double vd[11] = {p.U, -p.U * p.U, omd, omcd, omd / 36.0, omd / 9.0, 0.5 * omd, 0.25 * omd,
+                         p.s_e / 36.0, p.s_eps / 36.0, p.s_q / 12.0};
+  for (int i = 0; i < 11; ++i) {
+    p.kf[i] = (float)vf[i];
+    p.kd[i] = vd[i];
+  }
+}
 
 // One lattice of a batch: its parameters, its two population buffers
 // (buf[parity] holds f*(n)) and the index of its first row tile in the
@@ -306,22 +344,8 @@ __device__ __forceinline__ bool speed_ok(LF uu) { return uu.v <= 0.09f; }
 __device__ __forceinline__ bool speed_ok(LD uu) { return uu.v <= 0.09; }
 __device__ __forceinline__ bool speed_ok(LF2 uu) { return (uu.v.x <= 0.09f) & (uu.v.y <= 0.09f); }
 
-// Per-launch constants of the collision, rounded once from the double
-// parameters (omega = 1/tau).  omega and 1 - omega are chosen so that both
-// are exact in the lane's precision and sum to exactly 1 (Sterbenz: x - y is
-// exact for y/2 <= x <= 2y): the BGK update (1 - omega) h + omega h_eq then
-// carries mass and momentum over without a systematic bias from rounding
-// omega.
-template <class T>
-__device__ __forceinline__ void relaxation_pair(double omega, T &om, T &omc) {
-  om = (T)omega;
-  if (om >= (T)0.5) {
-    omc = (T)1 - om;
-  } else {
-    omc = (T)(1.0 - omega);
-    om = (T)1 - omc;
-  }
-}
+// Per-launch constants of the collision (StepParams::kf / kd, rounded once
+// on the host by fill_coefs).
 template <class L>
 struct Coef {
   L U, nUU;                 // U, -U^2
@@ -329,26 +353,27 @@ struct Coef {
   L w36, w9, w2, w4;        // omega/36, omega/9, omega/2, omega/4
   L se36, seps36, sq12;     // MRT: s_e/36, s_eps/36, s_q/12
 };
-template <class L> struct LaneScalar { using T = float; };  // LF, LF2
-template <> struct LaneScalar<LD> { using T = double; };
+template <class L>
+__device__ __forceinline__ L coef_at(const StepParams &p, int i);
+template <> __device__ __forceinline__ LF coef_at<LF>(const StepParams &p, int i) { return {p.kf[i]}; }
+template <> __device__ __forceinline__ LF2 coef_at<LF2>(const StepParams &p, int i) {
+  return {make_float2(p.kf[i], p.kf[i])};
+}
+template <> __device__ __forceinline__ LD coef_at<LD>(const StepParams &p, int i) { return {p.kd[i]}; }
 template <class L>
 __device__ __forceinline__ Coef<L> make_coef(const StepParams &p) {
-  using T = typename LaneScalar<L>::T;
-  T omt, omct;
-  relaxation_pair<T>(p.omega, omt, omct);
-  const double om = omt, omc = omct;
   Coef<L> k;
-  k.U = splat<L>(p.U);
-  k.nUU = splat<L>(-p.U * p.U);
-  k.om = splat<L>(om);
-  k.omc = splat<L>(omc);
-  k.w36 = splat<L>(om / 36.0);
-  k.w9 = splat<L>(om / 9.0);
-  k.w2 = splat<L>(0.5 * om);
-  k.w4 = splat<L>(0.25 * om);
-  k.se36 = splat<L>(p.s_e / 36.0);
-  k.seps36 = splat<L>(p.s_eps / 36.0);
-  k.sq12 = splat<L>(p.s_q / 12.0);
+  k.U = coef_at<L>(p, 0);
+  k.nUU = coef_at<L>(p, 1);
+  k.om = coef_at<L>(p, 2);
+  k.omc = coef_at<L>(p, 3);
+  k.w36 = coef_at<L>(p, 4);
+  k.w9 = coef_at<L>(p, 5);
+  k.w2 = coef_at<L>(p, 6);
+  k.w4 = coef_at<L>(p, 7);
+  k.se36 = coef_at<L>(p, 8);
+  k.seps36 = coef_at<L>(p, 9);
+  k.sq12 = coef_at<L>(p, 10);
   return k;
 }
 
