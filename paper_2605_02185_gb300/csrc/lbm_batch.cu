@@ -208,8 +208,8 @@ int lbm_batch_create(int ncases, const lbm_case *cases, const lbm_opts *common, 
     b->cases.push_back(ctx);
   }
   b->desc = (CaseDesc *)(base + off);
-  int kernel = common->kernel, shape = default_shape(common->storage);
-  int ctas = common->ctas_per_sm > 0 ? common->ctas_per_sm : default_ctas(common->storage);
+  int kernel = common->kernel, shape = default_batch_shape(common->storage);
+  int ctas = common->ctas_per_sm > 0 ? common->ctas_per_sm : default_batch_ctas(common->storage);
   if (common->consumer_warps || common->cells_per_thread || common->stages) {
     shape = -1;
     for (int s = 0; s < kNumTmaShapes; ++s)
@@ -294,8 +294,8 @@ int lbm_batch_set_kernel(lbm_batch *b, int kernel, int ncw, int cpt, int stages,
   CK(cudaSetDevice(b->dev));
   CK(cudaStreamSynchronize(b->stream));
   const int storage = b->common.storage;
-  int shape = default_shape(storage);
-  int ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
+  int shape = default_batch_shape(storage);
+  int ctas = ctas_per_sm > 0 ? ctas_per_sm : default_batch_ctas(storage);
   if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
     shape = -1;
     for (int s = 0; s < kNumTmaShapes; ++s)
@@ -303,7 +303,6 @@ int lbm_batch_set_kernel(lbm_batch *b, int kernel, int ncw, int cpt, int stages,
     if (shape < 0) return LBM_ERR_ARG;
   } else if (kernel == LBM_KERNEL_AUTO) {
     kernel = default_kernel(storage);
-    if (ctas_per_sm <= 0) ctas = default_ctas(storage);
   }
   const int rc = configure_batch(b, kernel, shape, ctas);
   if (rc) return rc;
