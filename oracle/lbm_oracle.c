@@ -38,6 +38,10 @@
  *     column nx-1 after the other boundary rules.
  *   - Boundary order: top row, bottom row (all x), inlet column, outlet
  *     column (all y).
+ *   - Interpolated bounce-back (optional, Section 2.4's link-wise
+ *     alternative): Bouzidi-Firdaouss-Lallemand linear interpolation with
+ *     the link fraction q of the body's true surface; force by momentum
+ *     exchange of the leaving and returning populations.
  *   - Momentum exchange (Eq. 14): for a resting half-way wall
  *     f_in = f_out = f*_i(x), so each fluid-to-solid link (c_i pointing into
  *     the solid) adds 2 f*_i(x) c_i; the sum is the force on the solid.
@@ -91,6 +95,7 @@ typedef struct {
   double *f;            /* populations after stream + boundaries, f(n) */
   double *fs;           /* post-collision populations, f*(n) */
   double *rowF;         /* [ny][2] per-row force partial sums */
+  double *qlink;        /* [9][ny][nx] link fractions q(x, i) (interpolated bounce-back), NULL: half-way */
 } orc_t;
 
 #define IDX(o, k, x, y) ((((size_t)(k)) * (size_t)(o)->ny + (size_t)(y)) * (size_t)(o)->nx + (size_t)(x))
@@ -251,6 +256,7 @@ void orc_destroy(orc_t *o) {
   free(o->f);
   free(o->fs);
   free(o->rowF);
+  free(o->qlink);
   free(o);
 }
 
@@ -348,6 +354,114 @@ void orc_force(orc_t *o, double *F) {
   F[1] = fy;
 }
 
+/* Interpolated bounce-back (Section 2.4: the link-wise alternative to the
+ * staircase, after Bouzidi, Firdaouss and Lallemand 2001), linear form, for
+ * the population arriving at fluid node x in direction k from the solid
+ * side.  It left x in direction i = opp(k) and met the wall a fraction q of
+ * the link from x:
+ *   q <  1/2:  f_k(x) = 2q f*_i(x) + (1 - 2q) f*_i(x - c_i),
+ *   q >= 1/2:  f_k(x) = f*_i(x) / (2q) + (1 - 1/(2q)) f*_k(x);
+ * q = 1/2 is the half-way rule.  Where q < 1/2 and x - c_i is not a fluid
+ * node of the lattice, the half-way rule is used. */
+static double interpolated_bounce(const orc_t *o, int x, int y, int k) {
+  int i = opposite(k);
+  double q = o->qlink[IDX(o, i, x, y)];
+  int bx, by;
+  if (q < 0.5) {
+    if (!neighbour(o, x, y, i, -1, &bx, &by) || o->solid[(size_t)by * o->nx + bx])
+      return o->fs[IDX(o, i, x, y)];
+    return 2.0 * q * o->fs[IDX(o, i, x, y)] + (1.0 - 2.0 * q) * o->fs[IDX(o, i, bx, by)];
+  }
+  return o->fs[IDX(o, i, x, y)] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * o->fs[IDX(o, k, x, y)];
+}
+
+/* Link fractions for interpolated bounce-back: q[(i * ny + y) * nx + x] for
+ * fluid x with x + c_i solid (other entries ignored); NULL restores the
+ * half-way rule. */
+int orc_set_link_q(orc_t *o, const double *q) {
+  size_t n = 9 * (size_t)o->nx * o->ny;
+  if (!q) {
+    free(o->qlink);
+    o->qlink = NULL;
+    return 0;
+  }
+  if (!o->qlink) o->qlink = (double *)malloc(n * sizeof(double));
+  if (!o->qlink) return -1;
+  memcpy(o->qlink, q, n * sizeof(double));
+  return 0;
+}
+
+/* Copy of the link fractions (zeros under the half-way rule). */
+void orc_get_link_q(const orc_t *o, double *q) {
+  size_t n = 9 * (size_t)o->nx * o->ny;
+  if (o->qlink)
+    memcpy(q, o->qlink, n * sizeof(double));
+  else
+    memset(q, 0, n * sizeof(double));
+}
+
+/* Link fractions of a circular body of centre (cx, cy) and radius r: for
+ * each link from fluid x along c_i into a solid node, q is the smallest
+ * t in (0, 1] with |x + t c_i - c| = r (0.5 where the circle does not cross
+ * the link, e.g. a solid node outside the circle). */
+int orc_set_circle_q(orc_t *o, double cx, double cy, double r) {
+  int nx = o->nx, ny = o->ny;
+  double *q = (double *)calloc(9 * (size_t)nx * ny, sizeof(double));
+  if (!q) return -1;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[(size_t)y * nx + x]) continue;
+      for (int i = 1; i < 9; ++i) {
+        int tx, ty;
+        if (!neighbour(o, x, y, i, +1, &tx, &ty) || !o->solid[(size_t)ty * nx + tx]) continue;
+        double dx = x - cx, dy = y - cy;
+        double a = (double)(CX[i] * CX[i] + CY[i] * CY[i]);
+        double b = dx * CX[i] + dy * CY[i];
+        double c = dx * dx + dy * dy - r * r;
+        double disc = b * b - a * c;
+        double t = disc >= 0.0 ? (-b - sqrt(disc)) / a : -1.0;
+        q[IDX(o, i, x, y)] = (t > 0.0 && t <= 1.0) ? t : 0.5;
+      }
+    }
+  int rc = orc_set_link_q(o, q);
+  free(q);
+  return rc;
+}
+
+/* Momentum exchange for interpolated bounce-back (Mei, Luo, Shyy 1999, as
+ * cited for Eq. 14): each fluid-to-solid link adds c_i (f*_i(x, n) +
+ * f_opp(i)(x, n+1)), the population that left and the one that came back;
+ * called after the stream and boundary phases of step n, it returns F(n).
+ * With q = 1/2 this is the 2 f*_i c_i of orc_force, summed in the same
+ * order. */
+void orc_force_interpolated(orc_t *o, double *F) {
+  int nx = o->nx, ny = o->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < ny; ++y) {
+    double fx = 0.0, fy = 0.0;
+    for (int x = 0; x < nx; ++x) {
+      if (o->solid[(size_t)y * nx + x]) continue;
+      for (int k = 1; k < 9; ++k) {
+        int tx, ty;
+        if (!neighbour(o, x, y, k, +1, &tx, &ty)) continue;
+        if (!o->solid[(size_t)ty * nx + tx]) continue;
+        double v = o->fs[IDX(o, k, x, y)] + o->f[IDX(o, opposite(k), x, y)];
+        fx += v * CX[k];
+        fy += v * CY[k];
+      }
+    }
+    o->rowF[2 * y] = fx;
+    o->rowF[2 * y + 1] = fy;
+  }
+  double fx = 0.0, fy = 0.0;
+  for (int y = 0; y < ny; ++y) {
+    fx += o->rowF[2 * y];
+    fy += o->rowF[2 * y + 1];
+  }
+  F[0] = fx;
+  F[1] = fy;
+}
+
 /* Streaming phase (left side of Eq. 2), pull form, with half-way bounce-back
  * on solid sources and the placeholder for sources outside the lattice. */
 void orc_stream(orc_t *o) {
@@ -362,7 +476,7 @@ void orc_stream(orc_t *o) {
         if (!neighbour(o, x, y, k, -1, &sx, &sy))
           v = o->fs[IDX(o, k, x, y)];
         else if (o->solid[(size_t)sy * nx + sx])
-          v = o->fs[IDX(o, opposite(k), x, y)];
+          v = o->qlink ? interpolated_bounce(o, x, y, k) : o->fs[IDX(o, opposite(k), x, y)];
         else
           v = o->fs[IDX(o, k, sx, sy)];
         o->f[IDX(o, k, x, y)] = v;
@@ -493,19 +607,22 @@ void orc_boundaries(orc_t *o) {
 }
 
 /* One time step n -> n+1 in the paper's order (Section 2.1): collide, the
- * force of Eq. 14 from f*(n), stream, boundary corrections.  Fhist receives
+ * force of Eq. 14 from f*(n), stream, boundary corrections.  With
+ * interpolated bounce-back the force of step n is taken after the stream
+ * and boundary phases (it needs the returning populations).  Fhist receives
  * (Fx, Fy) of each step if not NULL. */
 void orc_run(orc_t *o, long nsteps, double *Fhist) {
   for (long s = 0; s < nsteps; ++s) {
     double F[2];
     orc_collide(o);
-    orc_force(o, F);
+    if (!o->qlink) orc_force(o, F);
+    orc_stream(o);
+    orc_boundaries(o);
+    if (o->qlink) orc_force_interpolated(o, F);
     if (Fhist) {
       Fhist[2 * s] = F[0];
       Fhist[2 * s + 1] = F[1];
     }
-    orc_stream(o);
-    orc_boundaries(o);
   }
 }
 

@@ -50,6 +50,10 @@ def _bind(lib):
     lib.orc_destroy.argtypes = [p]
     lib.orc_set_body_force.argtypes = [p, d, d]
     lib.orc_set_wall_velocity.argtypes = [p, d, d]
+    lib.orc_set_link_q.argtypes = [p, p]
+    lib.orc_set_circle_q.argtypes = [p, d, d, d]
+    lib.orc_force_interpolated.argtypes = [p, p]
+    lib.orc_get_link_q.argtypes = [p, p]
     lib.orc_init_equilibrium.argtypes = [p, p, p, p]
     for name in ("orc_set_f", "orc_get_f", "orc_set_fs", "orc_get_fs"):
         getattr(lib, name).argtypes = [p, p]
@@ -182,6 +186,25 @@ class Oracle:
 
     def set_collision(self, model, s_e=1.1, s_eps=1.1, s_q=1.1):
         self.lib.orc_set_collision(self.h, int(model), float(s_e), float(s_eps), float(s_q))
+
+    def set_link_q(self, q):
+        """Interpolated bounce-back with link fractions q[9, ny, nx] (None: half-way)."""
+        if q is None:
+            self.lib.orc_set_link_q(self.h, None)
+            return
+        q = np.ascontiguousarray(q, np.float64)
+        assert q.shape == (9, self.ny, self.nx)
+        self.lib.orc_set_link_q(self.h, q.ctypes.data)
+
+    def set_circle_q(self, xc, yc, r):
+        """Interpolated bounce-back on a circle of centre (xc, yc), radius r."""
+        self.lib.orc_set_circle_q(self.h, float(xc), float(yc), float(r))
+
+    def link_q(self) -> np.ndarray:
+        """Link fractions [9, ny, nx] (zeros under the half-way rule)."""
+        out = np.zeros((9, self.ny, self.nx))
+        self.lib.orc_get_link_q(self.h, out.ctypes.data)
+        return out
 
     def set_wall_velocity(self, uw_top, uw_bot):
         """Wall speeds of the constant-velocity bounce-back (Y_MOVING); both U by default."""

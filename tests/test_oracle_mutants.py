@@ -79,6 +79,18 @@ def equilibrium_second_moment_ok(lib):
             and abs((f * cx * cy).sum() - rho * ux * uy) <= 4e-16)
 
 
+def channel_q_converges(lib, q=0.25):
+    import test_oracle_interpolated as I
+    e1, e2 = I.channel_q(8, q, lib=lib, max_steps=60_000)[0], I.channel_q(16, q, lib=lib, max_steps=120_000)[0]
+    return 3.3 < e1 / e2 < 4.7
+
+
+def channel_q_force_balance(lib, q=0.25):
+    import test_oracle_interpolated as I
+    _, fx, total = I.channel_q(12, q, lib=lib, max_steps=120_000)
+    return abs(fx - total) <= 1e-9 * total
+
+
 def couette_exact(lib, rho0=1.0):
     ny, ut, ub = 16, 0.05, -0.02
     _, u, _ = P.couette(ny, ut, ub, rho0, steps=12_000, lib=lib)
@@ -106,7 +118,8 @@ MUTANTS = [
      lambda lib: uniform_stream_error(lib, O.Y_ZOUHE) <= 1e-13),
     ("inlet_coefficient", "(2.0 / 3.0) * rho * U", "(1.0 / 3.0) * rho * U",
      lambda lib: uniform_stream_error(lib, O.Y_FREESLIP) <= 1e-13),
-    ("bounce_back_not_reversed", "v = o->fs[IDX(o, opposite(k), x, y)];", "v = o->fs[IDX(o, k, x, y)];",
+    ("bounce_back_not_reversed", "interpolated_bounce(o, x, y, k) : o->fs[IDX(o, opposite(k), x, y)];",
+     "interpolated_bounce(o, x, y, k) : o->fs[IDX(o, k, x, y)];",
      lambda lib: P.poiseuille(8, 0.8, lib=lib, max_steps=40_000)[0] < 0.009),
     ("force_factor", "double v = 2.0 * o->fs", "double v = 1.0 * o->fs",
      lambda lib: abs(flat_wall_force(lib)[1] + 2.0) <= 1e-12),
@@ -123,6 +136,12 @@ MUTANTS = [
     ("moving_wall_sign", "fs[k] - 2.0 * WT[k] * rho", "fs[k] + 2.0 * WT[k] * rho", couette_exact),
     ("moving_wall_unit_density", "WT[k] * rho * (CX[k] * uw)", "WT[k] * 1.0 * (CX[k] * uw)",
      lambda lib: couette_exact(lib, rho0=1.5)),
+    ("interp_drops_behind_node", "+ (1.0 - 2.0 * q) * o->fs[IDX(o, i, bx, by)]", "+ 0.0 * o->fs[IDX(o, i, bx, by)]",
+     channel_q_converges),
+    ("interp_far_branch_weight", "o->fs[IDX(o, i, x, y)] / (2.0 * q) +", "o->fs[IDX(o, i, x, y)] / (2.0 * 0.5) +",
+     lambda lib: channel_q_converges(lib, q=0.7)),
+    ("interp_force_one_sided", "double v = o->fs[IDX(o, k, x, y)] + o->f[IDX(o, opposite(k), x, y)];",
+     "double v = 2.0 * o->fs[IDX(o, k, x, y)];", channel_q_force_balance),
     ("moving_wall_not_reversed", "if (CY[k] == into) f[opposite(k)] = fs[k]", "if (CY[k] == into) f[k] = fs[k]",
      couette_exact),
 ]
