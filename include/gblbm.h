@@ -98,7 +98,26 @@ typedef struct lbm_opts {
   int collision;       /* LBM_COLLIDE_BGK (Eq. 2) or LBM_COLLIDE_MRT (Eq. 6) */
   double s_e, s_eps, s_q; /* MRT rates of the e, epsilon and q moments (paper: 1.1 each);
                              the stress moments relax at 1/tau, rho and j are conserved */
+  int bounce;          /* LBM_BOUNCE_HALFWAY or LBM_BOUNCE_INTERPOLATED */
+  double body_xc, body_yc, body_r; /* LBM_BOUNCE_INTERPOLATED: the body's true surface, a circle
+                                      (nodes at integer coordinates); the mask stays the solid set */
 } lbm_opts;
+
+/* ---- body bounce-back (Section 2.4) ---------------------------------------
+ * HALFWAY: the staircase rule the paper uses, f_i(x, n+1) = f*_opp(i)(x, n).
+ * INTERPOLATED: the link-wise alternative the paper names (Bouzidi, Firdaouss
+ * and Lallemand, linear): a population leaving fluid node x along c_i meets
+ * the circle a fraction q of the link from x and returns as
+ *   q <  1/2:  2q f*_i(x) + (1 - 2q) f*_i(x - c_i),
+ *   q >= 1/2:  f*_i(x)/(2q) + (1 - 1/(2q)) f*_opp(i)(x).
+ * Its momentum exchange adds c_i (f*_i(x, n) + f_opp(i)(x, n+1)) per link, so
+ * the force of step n is known only after step n+1: with INTERPOLATED the
+ * history is empty after lbm_init_fields and holds F(0..k-1) after k steps
+ * (HALFWAY: F(0..k)).  Single lattices only (not batches, not
+ * lbm_step_noalloc), always on the direct step kernel (LBM_KERNEL_DIRECT
+ * whatever opts.kernel asks), so that the TMA kernels carry no code for it. */
+#define LBM_BOUNCE_HALFWAY 0
+#define LBM_BOUNCE_INTERPOLATED 1
 
 /* Defaults: F32 storage, BGK, MRT rates 1.1, auto kernel, free-slip,
  * capacity 1 << 20. */

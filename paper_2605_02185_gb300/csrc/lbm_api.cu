@@ -27,7 +27,8 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   const int elem = elem_size(o->storage);
   const int pitch = (int)align_up((size_t)o->nx, 64);
   const size_t pop = align_up((size_t)9 * o->ny * pitch * elem, kAlign);
-  const size_t lmap = align_up(std::max<size_t>(g.lmap.size(), 1) * sizeof(uint16_t), kAlign);
+  const size_t lmap = align_up(std::max<size_t>(g.lmap.size(), 1) * sizeof(uint16_t), kAlign) +
+                      align_up(g.qmap.size() * sizeof(float), kAlign);  // link fractions follow the map
   int slot_cap = 1;
   if (g.fx1 >= g.fx0) slot_cap = (g.fy1 - g.fy0 + 1) * (g.fx1 / 256 - g.fx0 / 256 + 1);
   const size_t slots = align_up((size_t)slot_cap * sizeof(double2), kAlign);
@@ -65,6 +66,7 @@ int find_shape(int kernel, int ncw, int cpt, int stages) {
 // slots) and capture the multi-step graph.
 int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
   if (kernel == LBM_KERNEL_AUTO) kernel = LBM_KERNEL_TMA;
+  if (c->qmap) kernel = LBM_KERNEL_DIRECT;  // interpolated bounce-back: direct kernel only
   int seg;
   if (kernel == LBM_KERNEL_DIRECT) {
     seg = kDirectThreads;
@@ -225,6 +227,9 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   c->buf[0] = base + offs[0];
   c->buf[1] = base + offs[1];
   c->lmap = (uint16_t *)(base + offs[2]);
+  c->qmap = c->geo.qmap.empty()
+                ? nullptr
+                : (float *)(base + offs[2] + align_up(std::max<size_t>(c->geo.lmap.size(), 1) * sizeof(uint16_t), kAlign));
   c->slots = (double2 *)(base + offs[3]);
   c->hist = (double *)(base + offs[4]);
   c->ctrl = (unsigned *)(base + offs[5]);
@@ -241,6 +246,9 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
       cudaMemcpyAsync(c->lmap, c->geo.lmap.data(), c->geo.lmap.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
                       c->stream) != cudaSuccess)
     return fail(LBM_ERR_CUDA);
+  if (c->qmap && cudaMemcpyAsync(c->qmap, c->geo.qmap.data(), c->geo.qmap.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return fail(LBM_ERR_CUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(LBM_ERR_CUDA);
   c->D_ref = o->D_ref > 0 ? o->D_ref : (c->geo.solid_rows > 1 ? c->geo.solid_rows - 1 : 1);
   c->rho_in = o->rho_in > 0 ? o->rho_in : 1.0;
@@ -254,6 +262,7 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.omega = 1.0 / o->tau;
   p.U = o->U;
   p.lmap = c->lmap;
+  p.qmap = c->qmap;
   p.lx0 = c->geo.lx0;
   p.ly0 = c->geo.ly0;
   p.lw = c->geo.lw;
@@ -328,7 +337,7 @@ int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u, const double
   }
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
   CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
-  CK(c->ops->force(c->buf[0], c->p, c->stream));
+  if (!c->qmap) CK(c->ops->force(c->buf[0], c->p, c->stream));  // interpolated: F(0) comes with step 1
   CK(cudaStreamSynchronize(c->stream));
   c->inited = true;
   return LBM_OK;
@@ -341,7 +350,7 @@ int lbm_init_fields_device(lbm_ctx *c, const float *rho, const float *u, const f
   CK(c->ops->init_device(c->buf[0], c->p, rho, u, v, with_noneq ? 1 : 0, 1.0 / c->p.omega, c->stream));
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
   CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
-  CK(c->ops->force(c->buf[0], c->p, c->stream));
+  if (!c->qmap) CK(c->ops->force(c->buf[0], c->p, c->stream));  // interpolated: F(0) comes with step 1
   CK(cudaStreamSynchronize(c->stream));
   c->inited = true;
   return LBM_OK;

@@ -163,6 +163,7 @@ int lbm_batch_workspace_bytes(int ncases, const lbm_case *cases, const lbm_opts 
 int lbm_batch_create(int ncases, const lbm_case *cases, const lbm_opts *common, lbm_batch **out) {
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
+  if (common && common->bounce != LBM_BOUNCE_HALFWAY) return LBM_ERR_ARG;  // single lattices only
   std::vector<size_t> sizes;
   size_t total = 0;
   int rc = batch_sizes(ncases, cases, common, &sizes, &total);

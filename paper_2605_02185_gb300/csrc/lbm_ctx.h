@@ -17,6 +17,7 @@ namespace gblbm {
 struct Geometry {
   int lx0 = 0, ly0 = 0, lw = 0, lh = 0;
   std::vector<uint16_t> lmap;
+  std::vector<float> qmap;  // interpolated bounce-back: [lh][lw][8] fractions per arriving direction
   double fconst_x = 0.0, fconst_y = 0.0;
   int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1;  // link-owning fluid nodes
   int solid_rows = 0;
@@ -39,6 +40,7 @@ struct lbm_ctx {
   void *buf[2] = {nullptr, nullptr};
   int cur = 0;  // buf[cur] holds the current f*
   uint16_t *lmap = nullptr;
+  float *qmap = nullptr;
   double2 *slots = nullptr;
   int slot_cap = 0;
   double *hist = nullptr;

@@ -109,6 +109,7 @@ struct StepParams {
   double U;                // inlet / wall speed; also the reference velocity of h
   // link map over the region [lx0, lx0+lw) x [ly0, ly0+lh)
   const uint16_t *lmap;
+  const float *qmap;            // interpolated bounce-back fractions [lh][lw][8], or null (half-way)
   int lx0, ly0, lw, lh;
   // row tiles: item t -> row t / nseg, segment t % nseg of seg cells
   int seg, nseg;
@@ -199,9 +200,17 @@ __device__ __forceinline__ bool plain_span(const StepParams &p, int xa, int xb, 
 // itself, on h: h*_opp(k) + 6 w_k c_kx U (rho - 1) with rho the density of the
 // node's f*.  Regular sources come from fetch(k, sx, sy) -- a staged row tile
 // or HBM.
-template <class S, class Fetch>
+//
+// With INTERP (the direct kernel of a lattice that has link fractions,
+// p.qmap) a solid source instead takes the interpolated bounce-back
+// (Bouzidi, Firdaouss and Lallemand, linear) of the link's fraction q:
+//   q <  1/2:  2q f*_opp(k)(x) + (1 - 2q) f*_opp(k)(x + c_k),
+//   q >= 1/2:  f*_opp(k)(x) / (2q) + (1 - 1/(2q)) f*_k(x),
+// and, when fxy is given, adds the link's momentum exchange (the population
+// that left along c_opp(k) plus the one that returns) to fxy.
+template <class S, class Fetch, bool INTERP = false>
 __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &p, int xe, int y, uint32_t lm,
-                                     Fetch fetch, typename Store<S>::C h[9]) {
+                                     Fetch fetch, typename Store<S>::C h[9], double *fxy = nullptr) {
   using C = typename Store<S>::C;
   const size_t own = (size_t)y * p.pitch + xe;
   const C U = (C)p.U;
@@ -226,8 +235,32 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
       else
         h[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
     } else if (lm & (1u << k)) {
-      h[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
-      if (CX(k) != 0) h[k] += (C)(-6.0 * WD(k) * CX(k)) * U;
+      const C hi = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
+      if constexpr (!INTERP) {
+        h[k] = hi;
+        if (CX(k) != 0) h[k] += (C)(-6.0 * WD(k) * CX(k)) * U;
+      } else {
+        // the weights of the f-form sum to 1, so on h the reference part
+        // r_opp(k) - r_k = -6 w_k c_kx U enters with the weight of f*_opp(k)(x)
+        const float q = __ldg(p.qmap + ((size_t)(y - p.ly0) * p.lw + (xe - p.lx0)) * 8 + (k - 1));
+        C v, wref;
+        if (q < 0.5f) {
+          const C hb = fetch(OPP(k), xe + CX(k), y + CY(k));  // the node behind, x + c_k
+          v = (C)(2.f * q) * hi + (C)(1.f - 2.f * q) * hb;
+          wref = (C)1;
+        } else {
+          const C a = (C)(0.5f / q);
+          v = a * hi + ((C)1 - a) * Store<S>::ld(A[(size_t)k * p.plane + own]);
+          wref = a;
+        }
+        if (CX(k) != 0) v += (C)(-6.0 * WD(k) * CX(k)) * U * wref;
+        h[k] = v;
+        if (fxy) {
+          const double m = (double)hi + (double)v;
+          fxy[0] += m * CX(OPP(k));
+          fxy[1] += m * CY(OPP(k));
+        }
+      }
     } else {
       h[k] = fetch(k, sx, sy);
     }

@@ -52,7 +52,24 @@ inline int check_opts(const lbm_opts *o) {
   if (o->collision == LBM_COLLIDE_MRT &&
       !(o->s_e > 0.0 && o->s_e < 2.0 && o->s_eps > 0.0 && o->s_eps < 2.0 && o->s_q > 0.0 && o->s_q < 2.0))
     return LBM_ERR_ARG;
+  if (o->bounce != LBM_BOUNCE_HALFWAY && o->bounce != LBM_BOUNCE_INTERPOLATED) return LBM_ERR_ARG;
+  if (o->bounce == LBM_BOUNCE_INTERPOLATED && !(o->body_r > 0.0 && std::isfinite(o->body_xc) &&
+                                                std::isfinite(o->body_yc) && std::isfinite(o->body_r)))
+    return LBM_ERR_ARG;
   return LBM_OK;
+}
+
+// Fraction q of the link from (x, y) along c_i at which it meets the circle
+// (cx, cy, r): the smallest t in (0, 1] with |(x, y) + t c_i - c| = r; 1/2
+// where the circle does not cross the link.
+inline float circle_fraction(int x, int y, int i, double cx, double cy, double r) {
+  const double dx = x - cx, dy = y - cy;
+  const double a = (double)(CX(i) * CX(i) + CY(i) * CY(i));
+  const double b = dx * CX(i) + dy * CY(i);
+  const double c = dx * dx + dy * dy - r * r;
+  const double disc = b * b - a * c;
+  const double t = disc >= 0.0 ? (-b - std::sqrt(disc)) / a : -1.0;
+  return (float)((t > 0.0 && t <= 1.0) ? t : 0.5);
 }
 
 inline int build_geometry(const lbm_opts *o, const uint8_t *mask, Geometry *g) {
@@ -80,6 +97,8 @@ inline int build_geometry(const lbm_opts *o, const uint8_t *mask, Geometry *g) {
   g->lw = x1 - x0 + 3;
   g->lh = y1 - y0 + 3;
   g->lmap.assign((size_t)g->lw * g->lh, 0);
+  const bool interp = o->bounce == LBM_BOUNCE_INTERPOLATED;
+  if (interp) g->qmap.assign((size_t)g->lw * g->lh * 8, 0.5f);
   auto solid = [&](int x, int y) { return mask[(size_t)y * nx + x] != 0; };
   long double fcx = 0.0L, fcy = 0.0L;
   for (int j = 0; j < g->lh; ++j)
@@ -100,10 +119,24 @@ inline int build_geometry(const lbm_opts *o, const uint8_t *mask, Geometry *g) {
           g->fy1 = std::max(g->fy1, y);
           for (int d = 1; d < 9; ++d)
             if (m & (1u << OPP(d))) {  // d points into the solid
-              fcx += 2.0L * (long double)ref_pop(d, o->U) * CX(d);
-              fcy += 2.0L * (long double)ref_pop(d, o->U) * CY(d);
+              // reference part of the link's momentum exchange: 2 r_d c_d
+              // (half-way) or (r_d + r_opp(d)) c_d (interpolated)
+              const long double rr = interp ? (long double)ref_pop(d, o->U) + (long double)ref_pop(OPP(d), o->U)
+                                            : 2.0L * (long double)ref_pop(d, o->U);
+              fcx += rr * CX(d);
+              fcy += rr * CY(d);
               ++g->links;
             }
+          if (interp) {
+            for (int k = 1; k < 9; ++k) {
+              if (!(m & (1u << k))) continue;
+              // arriving direction k left x along i = opp(k); below q = 1/2
+              // the node behind, x + c_k, must be fluid, else half-way
+              float q = circle_fraction(x, y, OPP(k), o->body_xc, o->body_yc, o->body_r);
+              if (q < 0.5f && solid(x + CX(k), y + CY(k))) q = 0.5f;
+              g->qmap[((size_t)j * g->lw + i) * 8 + (k - 1)] = q;
+            }
+          }
         }
       }
       g->lmap[(size_t)j * g->lw + i] = m;

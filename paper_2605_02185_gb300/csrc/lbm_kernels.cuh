@@ -80,8 +80,10 @@ __device__ __forceinline__ bool collide_node(typename Store<S>::C (&h)[9], const
 }
 
 // One node, general form: pull (with bounce-back and placeholders), boundary
-// rules, collision into h; adds the node's links to the force.
-template <int MRT, class S, class Fetch>
+// rules, collision into h; adds the node's links to the force.  With INTERP
+// (interpolated bounce-back) the links' momentum exchange is that of the
+// previous step, taken while pulling: it needs the returning populations.
+template <int MRT, class S, class Fetch, bool INTERP = false>
 __device__ __forceinline__ void node_compute(const S *__restrict__ A, const StepParams &p, int x, int y,
                                              const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
                                              bool &bad, typename Store<S>::C (&h)[9]) {
@@ -91,6 +93,13 @@ __device__ __forceinline__ void node_compute(const S *__restrict__ A, const Step
   if (lm & LM_SOLID) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) h[k] = (C)0;
+  } else if constexpr (INTERP) {
+    double fxy[2] = {0.0, 0.0};
+    pull<S, Fetch, true>(A, p, xe, y, lm, fetch, h, x == xe ? fxy : nullptr);
+    fx += fxy[0];
+    fy += fxy[1];
+    boundaries<C>(h, xe, y, p);
+    bad |= !collide_node<MRT, S>(h, cf);
   } else {
     pull<S>(A, p, xe, y, lm, fetch, h);
     boundaries<C>(h, xe, y, p);
@@ -117,12 +126,12 @@ __device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &
   for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
 }
 
-template <int MRT, class S, class Fetch>
+template <int MRT, class S, class Fetch, bool INTERP = false>
 __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
                                             int y, const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
                                             bool &bad) {
   typename Store<S>::C h[9];
-  node_compute<MRT, S>(A, p, x, y, cf, fetch, fx, fy, bad, h);
+  node_compute<MRT, S, Fetch, INTERP>(A, p, x, y, cf, fetch, fx, fy, bad, h);
   store_node<S>(B, p, x, y, h);
 }
 
@@ -214,10 +223,14 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   };
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
-    if (plain_span(p, xw, xw + 31, y))
+    if (plain_span(p, xw, xw + 31, y)) {
       update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
-    else if (x < x1)
-      update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+    } else if (x < x1) {
+      if (p.qmap)  // interpolated bounce-back is served by this kernel only
+        update_node<MRT, S, decltype(fetch), true>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+      else
+        update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+    }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_UNSTABLE);
   if (is_force_item(p, y, s))

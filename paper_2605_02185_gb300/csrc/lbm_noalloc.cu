@@ -52,6 +52,7 @@ int scratch_for_device(int dev, void **out) {
 
 extern "C" int lbm_step_noalloc(lbm_ctx *c, const void *f_in, void *f_out, double *force_out) {
   if (!c || !f_in || !f_out || !force_out || f_in == f_out) return LBM_ERR_ARG;
+  if (c->qmap) return LBM_ERR_ARG;  // interpolated bounce-back: the step's force needs the next step
   // Force tiles of the direct kernel (rows x 256-node tiles holding links).
   int fy0 = 0, fy1 = 0, fs0 = 0, fs1 = 0;
   const Geometry &g = c->geo;

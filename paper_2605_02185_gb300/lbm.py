@@ -26,6 +26,7 @@ LBM_BC_FREESLIP, LBM_BC_PERIODIC, LBM_BC_ZOUHE, LBM_BC_MOVINGWALL = 0, 1, 2, 3
 LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64 = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK = 0, 1, 2, 3
 LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
+LBM_BOUNCE_HALFWAY, LBM_BOUNCE_INTERPOLATED = 0, 1
 ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8}
 ELEM_NUMPY = {LBM_F32: np.float32, LBM_F16_OFS: np.float16, LBM_BF16_OFS: np.uint16, LBM_F64: np.float64}
 
@@ -50,6 +51,8 @@ class lbm_opts(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("collision", ctypes.c_int),
         ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
+        ("bounce", ctypes.c_int),
+        ("body_xc", ctypes.c_double), ("body_yc", ctypes.c_double), ("body_r", ctypes.c_double),
     ]
 
 
@@ -340,7 +343,7 @@ class Lattice:
     def __init__(self, nx, ny, tau, U, mask=None, bc=LBM_BC_FREESLIP, storage=LBM_F32, D_ref=0.0,
                  rho_in=1.0, kernel=LBM_KERNEL_AUTO, shape=None, ctas_per_sm=0, graph_steps=0,
                  history_capacity=1 << 20, stream=None, device=None, collision=LBM_COLLIDE_BGK,
-                 mrt_rates=(1.1, 1.1, 1.1)):
+                 mrt_rates=(1.1, 1.1, 1.1), bounce=LBM_BOUNCE_HALFWAY, body=None):
         import torch
 
         load_library()
@@ -360,6 +363,9 @@ class Lattice:
         o.graph_steps = int(graph_steps)
         o.collision = int(collision)
         o.s_e, o.s_eps, o.s_q = (float(v) for v in mrt_rates)
+        o.bounce = int(bounce)
+        if body is not None:
+            o.body_xc, o.body_yc, o.body_r = (float(v) for v in body)
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         nbytes = lbm_workspace_bytes(o, mask)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -440,9 +446,12 @@ class Lattice:
 
 
 def lattice_for(workload, **kw) -> Lattice:
-    """A Lattice for a ``workloads.Workload`` (its mask, tau, U, bc, D)."""
+    """A Lattice for a ``workloads.Workload`` (its mask, tau, U, bc, D; with
+    interpolated bounce-back its circle)."""
     kw.setdefault("bc", workload.bc)
     kw.setdefault("D_ref", float(workload.D))
+    if kw.get("bounce", LBM_BOUNCE_HALFWAY) == LBM_BOUNCE_INTERPOLATED:
+        kw.setdefault("body", (float(workload.xc), float(workload.yc), 0.5 * float(workload.D)))
     return Lattice(workload.nx, workload.ny, workload.tau, workload.U, mask=workload.mask(), **kw)
 
 

@@ -64,7 +64,7 @@ def test_host_only_entry_points(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(nx=4), dict(ny=3), dict(tau=0.5), dict(tau=0.4), dict(U=0.35), dict(U=-0.1),
-    dict(bc_top_bottom=4), dict(storage=7), dict(kernel=9),
+    dict(bc_top_bottom=4), dict(storage=7), dict(kernel=9), dict(bounce=2), dict(bounce=1, body_r=0.0),
 ])
 def test_argument_validation(lib, bad):
     from paper_2605_02185_gb300 import lbm

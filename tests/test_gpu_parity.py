@@ -257,6 +257,88 @@ def test_paired_16bit_tma_matches_direct(storage, mrt):
         assert np.array_equal(F, Fr), shape
 
 
+# ------------------------------------------------ interpolated bounce-back
+
+INTERP = dict(bounce=lbm.LBM_BOUNCE_INTERPOLATED)
+
+
+@functools.lru_cache(maxsize=16)
+def oracle_run_interpolated(wl: W.Workload, steps: int, mrt: bool = False):
+    """Oracle with interpolated bounce-back on the workload's circle: f*(steps),
+    forces F(0..steps-1) (each needs the next step's returning populations),
+    fields of f(steps)."""
+    o = O.Oracle(wl.nx, wl.ny, wl.tau, wl.U, bc_y=wl.bc, mask=wl.mask())
+    if mrt:
+        o.set_collision(O.MRT, *O.MRT_PAPER_RATES)
+    o.set_circle_q(wl.xc, wl.yc, wl.D / 2)
+    o.init_equilibrium(*wl.initial_fields())
+    F = o.run(steps)
+    fields = o.fields()
+    o.collide()
+    return o.get_fs(), F, fields
+
+
+def gpu_run_interpolated(wl, steps, **kw):
+    lat = lbm.lattice_for(wl, **INTERP, **kw)
+    try:
+        lat.init_fields(*wl.initial_fields())
+        assert lat.force_count() == 0
+        lat.step(steps)
+        lat.sync()
+        assert lat.force_count() == steps
+        pops, F, fields = lat.get_populations(), lat.forces_raw(0, steps), lat.fields()
+    finally:
+        lat.close()
+    return pops, F, fields
+
+
+def compare_interpolated(wl, steps, pops, F, fields, tol_f, tol_F, storage=lbm.LBM_F32, mrt=False):
+    fs, Fo, (ro, uo, vo) = oracle_run_interpolated(wl, steps, mrt)
+    fluid = wl.mask() == 0
+    f = offsets_to_f(pops, wl.U, storage)
+    r, u, v = fields
+    assert np.max(np.abs(f - fs)[:, fluid]) <= tol_f
+    assert max(np.max(np.abs(u - uo)[fluid]), np.max(np.abs(v - vo)[fluid])) <= tol_f
+    assert np.max(np.abs(r - ro)[fluid]) <= 3 * tol_f
+    assert np.max(np.abs(F - Fo)) <= tol_F * max(np.max(np.abs(Fo)), 1e-30)
+
+
+@pytest.mark.parametrize("size", [(37, 23), (300, 41)], ids=["37x23", "300x41"])
+def test_interpolated_bounce_back_matches_oracle(size):
+    """Bouzidi linear bounce-back with the circle's link fractions, and its
+    two-sided momentum exchange (history entry n written by step n + 1)."""
+    wl = W.random_case(size[0], size[1], seed=700 + size[0], bc=W.BC_FREESLIP, D=8)
+    pops, F, fields = gpu_run_interpolated(wl, 60)
+    compare_interpolated(wl, 60, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4)
+
+
+def test_interpolated_bounce_back_16bit_and_mrt():
+    wl = W.random_case(300, 41, seed=711, bc=W.BC_ZOUHE, D=8, tau=0.56)
+    pops, F, fields = gpu_run_interpolated(wl, 60, **MRT)
+    compare_interpolated(wl, 60, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
+    pops, F, fields = gpu_run_interpolated(wl, 60, storage=lbm.LBM_F16_OFS, **MRT)
+    compare_interpolated(wl, 60, pops, F, fields, tol_f=2e-3 * wl.U, tol_F=2e-2, storage=lbm.LBM_F16_OFS,
+                         mrt=True)
+
+
+def test_interpolated_small_cylinder_mrt():
+    """The C1 geometry with interpolated bounce-back and the paper's MRT:
+    1000 steps within max |u - u_ref| <= 1e-5 U, every force entry within
+    1e-4 of the oracle's."""
+    wl = W.PARITY_D10
+    pops, F, fields = gpu_run_interpolated(wl, 1000, **MRT)
+    compare_interpolated(wl, 1000, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
+
+
+def test_interpolated_bounce_back_runs_on_the_direct_kernel():
+    wl = W.random_case(97, 33, seed=3, bc=W.BC_FREESLIP, D=8)
+    lat = lbm.lattice_for(wl, kernel=lbm.LBM_KERNEL_TMA, **INTERP)
+    try:
+        assert lat.kernel_info()["kernel"] == lbm.LBM_KERNEL_DIRECT
+    finally:
+        lat.close()
+
+
 def test_every_tma_shape_matches_direct():
     wl = W.random_case(613, 57, seed=21, bc=W.BC_FREESLIP, D=10)
     ref, Fr, _, _ = gpu_run(wl, 30, kernel=lbm.LBM_KERNEL_DIRECT)
