@@ -99,3 +99,19 @@ def test_circle_fractions_lie_on_the_circle(orc):
         assert 0.0 < t <= 1.0
         px, py = x + t * cx[i] - wl.xc, y + t * cy[i] - wl.yc
         assert abs(np.hypot(px, py) - wl.D / 2) <= 1e-12
+
+
+def test_symmetric_body_at_rest_feels_no_force(orc):
+    # fluid at rest around a mirror-symmetric staircased circle with its
+    # link fractions: every step's two-sided momentum exchange cancels
+    nx, ny, D = 41, 41, 14
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    mask = (4 * ((xx - 20) ** 2 + (yy - 20) ** 2) <= D * D).astype(np.uint8)
+    o = O.Oracle(nx, ny, 0.7, 0.0, bc_y=O.Y_PERIODIC, bc_x=O.X_PERIODIC, mask=mask)
+    o.set_circle_q(20.0, 20.0, D / 2)
+    o.init_equilibrium(1.0, 0.0, 0.0)
+    F = o.run(20)
+    assert np.max(np.abs(F)) <= 1e-13
+    r, u, v = o.fields()
+    fluid = mask == 0
+    assert np.max(np.abs(u[fluid])) <= 1e-15 and np.max(np.abs(v[fluid])) <= 1e-15
