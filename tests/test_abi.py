@@ -96,3 +96,14 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_2605_02185_gb300 import lbm
     with pytest.raises(ImportError):
         lbm.load_library(str(tmp_path / "nope.so"))
+
+
+def test_every_network_symbol_is_exported(lib):
+    from paper_2605_02185_gb300 import lbm
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gbnn.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"^\s*int\s+(gbnn_\w+)\s*\(", src, flags=re.M)))
+    assert len(names) >= 12
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s(gbnn_\w+)", out))
+    assert not [n for n in names if n not in exported]
