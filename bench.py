@@ -484,8 +484,9 @@ def run_statistics(args):
     rows, total_nodes, total_s = [], 0, 0.0
     for bc, st in runs:
         wl = dataclasses.replace(base, bc=bc_ids[bc])
+        bounce = lbm.LBM_BOUNCE_INTERPOLATED if args.bounce == "interpolated" else lbm.LBM_BOUNCE_HALFWAY
         lat = lbm.lattice_for(wl, storage=st_ids[st], stream=stream, device=device, collision=coll,
-                              history_capacity=args.stat_steps + 16)
+                              history_capacity=args.stat_steps + 16, bounce=bounce)
         lat.init_fields(*wl.initial_fields())
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
@@ -515,7 +516,8 @@ def run_statistics(args):
             "value": total_nodes / total_s / 1e9, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
             "dtype": ",".join(sorted({st for _, st in runs})), "steps": args.stat_steps,
             "config": {"workload": base.name, "nx": base.nx, "ny": base.ny, "D": base.D, "U": base.U,
-                       "tau": base.tau, "Re": base.Re, "collision": args.collision, "window": args.window},
+                       "tau": base.tau, "Re": base.Re, "collision": args.collision, "window": args.window,
+                       "bounce": args.bounce},
             "runs": rows, "errors_vs_f64": errors}), flush=True)
     return 0
 
@@ -542,6 +544,8 @@ def main(argv=None):
     ap.add_argument("--D", type=int, default=0, help="statistics workload: cylinder diameter (default 80)")
     ap.add_argument("--U", type=float, default=0.0, help="statistics workload: inlet speed (default 0.05)")
     ap.add_argument("--Re", type=float, default=0.0, help="statistics workload: Reynolds number (default 100)")
+    ap.add_argument("--bounce", choices=["halfway", "interpolated"], default="halfway",
+                    help="statistics workload: body bounce-back (interpolated runs on the direct kernel)")
     ap.add_argument("--snapshots", type=int, default=20000, help="warmstart workload: training snapshots")
     ap.add_argument("--eval-cases", type=int, default=16, help="warmstart workload: held-out Re values")
     ap.add_argument("--cases", type=int, default=64, help="batch workload: number of cases")
