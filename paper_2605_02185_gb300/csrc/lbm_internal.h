@@ -43,6 +43,11 @@ struct KernelOps {
   int tma_pair;
 };
 
+// Look up (once per device) the address of lbm_step_noalloc's static
+// scratch array; lbm_create_ex calls it so that the lookup never happens
+// inside a no-allocation step.
+int noalloc_prepare(int dev);
+
 const KernelOps *ops_f32();
 const KernelOps *ops_f16();
 const KernelOps *ops_bf16();

@@ -50,6 +50,18 @@ int scratch_for_device(int dev, void **out) {
 
 }  // namespace
 
+namespace gblbm {
+
+// Called by lbm_create_ex with the context's device current: the address
+// lookup (which may load the module that holds the array) happens when the
+// context is made, so lbm_step_noalloc itself never triggers it.
+int noalloc_prepare(int dev) {
+  void *ptr = nullptr;
+  return scratch_for_device(dev, &ptr);
+}
+
+}  // namespace gblbm
+
 extern "C" int lbm_step_noalloc(lbm_ctx *c, const void *f_in, void *f_out, double *force_out) {
   if (!c || !f_in || !f_out || !force_out || f_in == f_out) return LBM_ERR_ARG;
   if (c->qmap) return LBM_ERR_ARG;  // interpolated bounce-back: the step's force needs the next step
