@@ -38,13 +38,17 @@ if ROOT not in sys.path:
 METRIC = "GLUPS + % HBM roofline (D2Q9 BGK cylinder); wall time to periodic Cd/Cl/St"
 UNIT = "GLUPS"
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel
-# on the 16000 x 8000 lattice, per storage form, from one ncu capture each,
-# with the kernel-source digest they were taken for; a figure is reported
-# only while the step kernel source is unchanged.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step kernel,
+# per node, per storage form, from one ncu capture each, with the
+# kernel-source digest they were taken for; a figure is reported only while
+# the step kernel source is unchanged.
 NCU_TRAFFIC = {"digest": "930760eecb3f4b1a",
-               "bytes_per_node": {"f32": (4712649216 + 4563177984) / 128e6, "f16": (2345245440 + 2256823040) / 128e6},
-               "capture": "profiles/step_tma_throughput_dram.md"}
+               "bytes_per_node": {"f32": (4712649216 + 4563177984) / 128e6, "f16": (2345245440 + 2256823040) / 128e6}}
+
+# The paper's own Re = 100 results (Table 2, "present work": MRT, D = 20,
+# U = 0.02, 800 x 400), quoted as context; the paper states no hardware.
+PAPER_TABLE2 = {"cd_mean": 1.4, "cl": 0.31, "st": 0.168,
+                "source": "Table 2 (present work, Re = 100, MRT, D = 20, U = 0.02); no hardware or timing stated"}
 
 
 # ----------------------------------------------------------------- helpers
@@ -333,10 +337,99 @@ def run_ours(args, workload):
         "clocks": clocks,
         "last_cd_cl": [cdv, clv],
     }
+    if not args.no_extras and world == 1:
+        line["extra"] = extras(args, workload, device, stream)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(workload, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_steps(step, steps: int, stream) -> float:
+    """Seconds of `steps` steps (CUDA events on the launching stream)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def extras(args, workload, device, stream):
+    """The rest of the headline metric in the same run: the 16-bit storage
+    forms on the same lattice, the batch of 64 cases (MRT), the wall time of
+    a cold start to periodic Cd/Cl/St on the 1600 x 800 grid, and the paper's
+    Table 2 values as context."""
+    import numpy as np
+    import torch
+    from paper_2605_02185_gb300 import lbm, postprocess
+    from paper_2605_02185_gb300 import workloads as W
+    out = {}
+    peak, src = measured_peaks()
+    steps = max(args.steps, 20)
+    rho0, u0, v0 = workload.initial_fields()
+    forms = {}
+    for name, st in (("f16", lbm.LBM_F16_OFS), ("bf16", lbm.LBM_BF16_OFS)):
+        lat = lbm.lattice_for(workload, storage=st, stream=stream, device=device)
+        lat.init_fields(rho0, u0, v0)
+        lat.step(args.warmup)
+        lat.sync()
+        dt = time_steps(lat.step, steps, stream)
+        lat.sync()
+        b = lat.bytes_per_step()
+        forms[name] = {"glups": workload.cells * steps / dt / 1e9, "bytes_per_node": b / workload.cells,
+                       "roofline_frac": b * steps / dt / 1e9 / peak, "kernel": lat.kernel_info()}
+        lat.close()
+    del rho0, u0, v0
+    torch.cuda.empty_cache()
+    out["storage_forms"] = {"workload": workload.name, "steps": steps, "peak_gbs": peak, "peak_source": src, **forms}
+
+    cases = W.batched_cases(64, seed=4)
+    b = lbm.Batch(cases, stream=stream, device=device, collision=lbm.LBM_COLLIDE_MRT)
+    b.init_all()
+    b.step(args.warmup)
+    torch.cuda.synchronize(device)
+    nodes, bytes_step = b.nodes()
+    dt = time_steps(b.step, steps, stream)
+    out["batch"] = {"workload": "64 cylinder cases, Re log-uniform in [60, 200], D in {20, 30, 40, 60}, "
+                                "40D x 20D, U = 0.05, free-slip, MRT (Eq. 6)",
+                    "nodes": nodes, "steps": steps, "glups": nodes * steps / dt / 1e9,
+                    "roofline_frac": bytes_step * steps / dt / 1e9 / peak, "kernel": b.kernel_info()}
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+
+    # cold start to periodic lift: the seeded +-1e-3 U perturbation of the
+    # resting-cylinder start, lift checked every `chunk` steps
+    wl = W.cylinder_case(40, 0.05, 80.0, seed=5, perturb=1e-3, name="cyl_Re80_D40_1600x800")
+    lat = lbm.lattice_for(wl, stream=stream, device=device, history_capacity=1 << 20)
+    chunk, max_steps, n, at = 2000, 400_000, 0, None
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    lat.init_fields(*wl.initial_fields())
+    cds, cls = [], []
+    while n < max_steps and at is None:
+        lat.step(chunk)
+        have = sum(len(c) for c in cls)
+        cd, cl = lat.forces(have, n + chunk + 1 - have)
+        n += chunk
+        cds.append(cd)
+        cls.append(cl)
+        at = postprocess.periodic_index(np.concatenate(cls))
+    t_wall = time.perf_counter() - t0
+    cd, cl = np.concatenate(cds), np.concatenate(cls)
+    lat.close()
+    row = {"workload": f"{wl.name}: Re = 80, D = 40, U = 0.05, tau = {wl.tau:.4f}, BGK, free-slip, "
+                       "seeded +-1e-3 U start", "periodic_at_step": at, "steps_run": n,
+           "wall_s": t_wall, "criterion": "lift amplitude >= 0.05 changing < 0.5 % per period, two periods"}
+    if at is not None:
+        row.update({k: v for k, v in postprocess.statistics(cd[:at + 1], cl[:at + 1], wl.D, wl.U, periods=2).items()
+                    if k in ("cd_mean", "cl_amp", "st")})
+    out["time_to_periodic"] = row
+    out["paper_table2"] = PAPER_TABLE2
+    return out
 
 
 def run_batch(args):
@@ -553,6 +646,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 16-bit forms, batch and time-to-periodic measurements of the default line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

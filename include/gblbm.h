@@ -196,6 +196,24 @@ int lbm_get_populations(lbm_ctx *ctx, void *dst, size_t bytes);
  * restored. */
 int lbm_set_populations(lbm_ctx *ctx, const void *src, size_t bytes, int64_t history_count);
 
+/* Self-describing checkpoint (no counterpart in the paper): an 88-byte header
+ * (magic "GBLBMCK1", version, nx, ny, storage, collision, top/bottom rule,
+ * bounce-back rule, tau, U, history count, stored history entries, payload
+ * bytes, 64-bit checksum), then the populations as lbm_get_populations
+ * writes them, then the force-history entries still in the ring (raw
+ * (Fx, Fy) doubles, oldest first).  The checksum is FNV-1a taken over the
+ * payload's little-endian 64-bit words.  All buffers are host memory owned
+ * by the caller.
+ *   lbm_checkpoint_bytes: the image size for the context's current state.
+ *   lbm_checkpoint_save:  write the image; bytes must equal that size.
+ *   lbm_checkpoint_load:  restore populations, step count and history.
+ *     LBM_ERR_ARG, with the context unchanged, when the image is truncated
+ *     or padded, its checksum does not match (corruption), or it describes
+ *     another lattice (size, storage, collision, rules, tau or U). */
+int lbm_checkpoint_bytes(lbm_ctx *ctx, size_t *bytes);
+int lbm_checkpoint_save(lbm_ctx *ctx, void *dst, size_t bytes);
+int lbm_checkpoint_load(lbm_ctx *ctx, const void *src, size_t bytes);
+
 /* A rectangular window [x0, x0+w) x [y0, y0+h) of the current f* offsets,
  * packed host [9][h][w] of the storage type (probes, sampled checks). */
 int lbm_get_window(lbm_ctx *ctx, int x0, int y0, int w, int h, void *dst);
@@ -213,6 +231,20 @@ int lbm_kernel_shapes(int *out, int cap, int *count);
 
 /* The same for LBM_KERNEL_TMA or LBM_KERNEL_TMA_BULK. */
 int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count);
+
+/* Failure-path testing (no counterpart in the paper).  Every wait of the
+ * step kernels on another warp or on an asynchronous copy is bounded; when
+ * one gives up, the step stops its remaining work, waits (bounded again)
+ * for its own copies in flight and returns, and lbm_sync reports
+ * LBM_ERR_TIMEOUT -- the GPU is never trapped or hung.  This call makes that
+ * path testable: the waits give up after wait_seconds (<= 0: the default
+ * 1 s; at most 60), and if tile >= 0 the TMA producer announces the copies
+ * of row tile `tile` (row * tiles per row + segment, as the kernel numbers
+ * them) but never issues them, so the waits on that tile run out.  The
+ * populations are then partly stale: restore a checkpoint or re-initialise.
+ * The context must use LBM_KERNEL_TMA or LBM_KERNEL_TMA_BULK (LBM_ERR_ARG
+ * otherwise).  tile < 0 and wait_seconds <= 0 restore normal operation. */
+int lbm_set_fault_injection(lbm_ctx *ctx, int64_t tile, double wait_seconds);
 
 /* The CUDA stream the context launches on (cudaStream_t). */
 int lbm_get_stream(lbm_ctx *ctx, void **stream);
@@ -241,9 +273,11 @@ int lbm_bytes_per_step(lbm_ctx *ctx, double *bytes);
  * Scratch (force partials and reduction counters) lives in a 1 MiB device
  * array inside the library, held by every GPU that loads the library until
  * the process exits.  Bodies whose link-owning nodes span more than 65,520
- * row tiles of 256 nodes are rejected with LBM_ERR_ARG.  The first call on a
- * device looks up the array's address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call clears and reuses the
+ * row tiles of 256 nodes are rejected with LBM_ERR_ARG.  lbm_create and
+ * lbm_create_ex look up the array's address on their device
+ * (cudaGetSymbolAddress, which may load the module holding it), so that
+ * lookup is done before this entry point is first called on a context of
+ * that device.  Every call clears and reuses the
  * same array: calls whose kernels overlap on the GPU (different streams, or
  * several contexts) race on it.  The |u| > 0.3 stability check is not
  * reported by this entry point.  No cudaMalloc, cudaFree or other
@@ -291,6 +325,14 @@ int lbm_batch_get_stream(lbm_batch *batch, void **stream);
 int lbm_batch_launch_count(lbm_batch *batch, int64_t *count);
 /* Total nodes of all cases, and the algorithmic HBM bytes of one batch step. */
 int lbm_batch_nodes(lbm_batch *batch, int64_t *nodes, double *bytes_per_step);
+
+/* Diagnostic (no counterpart in the paper): -1/x as the float collisions
+ * compute it (the hardware reciprocal estimate refined by one
+ * Newton-Raphson step, see Eq. 4's 1/rho), for x DEVICE float [n], into
+ * DEVICE y_single (one node per lane) and y_pair (packed pairs of nodes),
+ * asynchronously on `stream` (cudaStream_t).  Lets a test bound its error
+ * against the correctly rounded quotient. */
+int lbm_probe_neg_recip(const float *x, float *y_single, float *y_pair, int64_t n, void *stream);
 
 const char *lbm_error_string(int code);
 const char *lbm_version(void);

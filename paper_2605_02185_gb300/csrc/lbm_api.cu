@@ -213,6 +213,8 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   };
   if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(LBM_ERR_CUDA);
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) return fail(LBM_ERR_CUDA);
+  rc = noalloc_prepare(c->dev);
+  if (rc) return fail(rc);
   if (o->workspace) {
     if (o->workspace_bytes < c->ws_bytes || ((uintptr_t)o->workspace % kAlign) != 0) return fail(LBM_ERR_OOM);
     c->ws = o->workspace;
@@ -280,6 +282,8 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.s_eps = o->s_eps;
   p.s_q = o->s_q;
   fill_coefs(p);
+  p.wait_ns = 1000000000ull;  // every bounded device wait gives up after 1 s
+  p.fault_tile = -1;
 
   int shape = default_shape(o->storage);
   int kernel = o->kernel;
@@ -524,6 +528,18 @@ int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int cta
   }
   const int rc = configure_kernel(c, kernel, shape, ctas);
   if (rc) return rc;
+  return capture_graph(c);
+}
+
+int lbm_set_fault_injection(lbm_ctx *c, int64_t tile, double wait_seconds) {
+  if (!c) return LBM_ERR_ARG;
+  if (c->kernel != LBM_KERNEL_TMA && c->kernel != LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (tile >= (int64_t)c->ny * c->nseg || !(wait_seconds <= 60.0)) return LBM_ERR_ARG;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaStreamSynchronize(c->stream));
+  c->p.fault_tile = tile < 0 ? -1 : (int)tile;
+  c->p.wait_ns = wait_seconds > 0 ? (unsigned long long)(wait_seconds * 1e9) : 1000000000ull;
+  if (c->p.wait_ns == 0) c->p.wait_ns = 1;
   return capture_graph(c);
 }
 

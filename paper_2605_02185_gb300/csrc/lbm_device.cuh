@@ -130,6 +130,12 @@ struct StepParams {
   // s_eps/36, s_q/12: float for the float lanes, double for the double lane
   float kf[11];
   double kd[11];
+  // Failure-path controls: the limit of every bounded device wait (ns; 0
+  // reads as 1 s) and, for tests of that path only, one row tile whose
+  // copies the TMA producer announces but does not issue (-1: none), so the
+  // waits on it give up and the step reports ERR_TIMEOUT.
+  unsigned long long wait_ns;
+  int fault_tile;
 };
 
 // omega and 1 - omega rounded as a pair that is exact in T and sums to
@@ -604,15 +610,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ unsigned long long wait_limit(unsigned long long ns) {
+  return ns ? ns : 1000000000ull;
+}
 // Bounded wait: true when the phase with this parity completed; false after
-// ~1 s or as soon as *abort is set (then the caller skips its work).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort) {
+// limit_ns (0: 1 s) or as soon as *abort is set (then the caller skips its
+// work).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort,
+                                                  unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
+  const unsigned long long t0 = global_ns(), lim = wait_limit(limit_ns);
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > 1000000000ull) return false;
+    if (global_ns() - t0 > lim) return false;
   }
 }
 // 1-D bulk copy global -> shared, completion counted on an mbarrier.  Both

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
       int j = 0;
       for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
         const int st = j % STAGES;
-        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
           if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
           *s_abort = 1;
           break;
@@ -305,6 +305,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
         }
         const uint32_t fb = smem_addr(&bars[st]);
         mbar_arrive_expect_tx(fb, total);
+        if (t == p.fault_tile) continue;  // failure-path test: announced, never copied
         S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
         for (int k = 0; k < 9; ++k)
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
         const uint32_t fb = smem_addr(&bars[q % STAGES]);
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
-          if (global_ns() - t0 > 1000000000ull) {
+          if (global_ns() - t0 > wait_limit(p.wait_ns)) {
             atomicOr(p.err, ERR_TIMEOUT);
             break;
           }
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
     const int st = j % STAGES;
     bool ok = false;
     if (!*s_abort) {
-      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort, p.wait_ns);
       if (!ok && !*s_abort) {
         atomicOr(p.err, ERR_TIMEOUT);
         *s_abort = 1;
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
       int j = 0;
       for (long long t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
         const int st = j % STAGES;
-        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, cases[0].p.wait_ns)) {
           if (!*s_abort) atomicOr(cases[0].p.err, ERR_TIMEOUT);
           *s_abort = 1;
           break;
@@ -481,6 +482,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         info[st] = make_int4(c, y, s, 0);
         const uint32_t fb = smem_addr(&bars[st]);
         mbar_arrive_expect_tx(fb, total);
+        if (tl == p.fault_tile) continue;  // failure-path test: announced, never copied
         S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
         for (int k = 0; k < 9; ++k)
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         const uint32_t fb = smem_addr(&bars[q % STAGES]);
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
-          if (global_ns() - t0 > 1000000000ull) {
+          if (global_ns() - t0 > wait_limit(cases[0].p.wait_ns)) {
             atomicOr(cases[0].p.err, ERR_TIMEOUT);
             break;
           }
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
     const int st = j % STAGES;
     bool ok = false;
     if (!*s_abort) {
-      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort, cases[0].p.wait_ns);
       if (!ok && !*s_abort) {
         atomicOr(cases[0].p.err, ERR_TIMEOUT);
         *s_abort = 1;
@@ -625,7 +627,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
       int j = 0;
       for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
         const int st = j % STAGES;
-        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort)) {
+        if (j >= STAGES && !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
           if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
           *s_abort = 1;
           break;
@@ -646,6 +648,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         }
         const uint32_t fb = smem_addr(&bars[st]);
         mbar_arrive_expect_tx(fb, total);
+        if (t == p.fault_tile) continue;  // failure-path test: announced, never copied
         S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
         for (int k = 0; k < 9; ++k)
@@ -657,7 +660,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         const uint32_t fb = smem_addr(&bars[q % STAGES]);
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
-          if (global_ns() - t0 > 1000000000ull) {
+          if (global_ns() - t0 > wait_limit(p.wait_ns)) {
             atomicOr(p.err, ERR_TIMEOUT);
             break;
           }
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
     const int st = j % STAGES;
     bool ok = false;
     if (!*s_abort) {
-      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort);
+      ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort, p.wait_ns);
       if (!ok && !*s_abort) {
         atomicOr(p.err, ERR_TIMEOUT);
         *s_abort = 1;

@@ -107,6 +107,11 @@ def load_library(path: str | None = None):
         "lbm_launch_count": (i, [vp, ctypes.POINTER(i64)]),
         "lbm_bytes_per_step": (i, [vp, ctypes.POINTER(d)]),
         "lbm_step_noalloc": (i, [vp, vp, vp, vp]),
+        "lbm_set_fault_injection": (i, [vp, i64, d]),
+        "lbm_checkpoint_bytes": (i, [vp, ctypes.POINTER(sz)]),
+        "lbm_checkpoint_save": (i, [vp, vp, sz]),
+        "lbm_checkpoint_load": (i, [vp, vp, sz]),
+        "lbm_probe_neg_recip": (i, [vp, vp, vp, i64, vp]),
         "lbm_batch_workspace_bytes": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(sz)]),
         "lbm_batch_create": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(vp)]),
         "lbm_batch_destroy": (None, [vp]),
@@ -293,6 +298,33 @@ def lbm_step_noalloc(h, f_in_ptr: int, f_out_ptr: int, force_out_ptr: int):
                                            ctypes.c_void_p(force_out_ptr)), "lbm_step_noalloc")
 
 
+def lbm_set_fault_injection(h, tile: int, wait_seconds: float):
+    """Failure-path test control (see gblbm.h): bounded-wait limit and a row
+    tile whose copies are announced but never issued (tile < 0: none)."""
+    _check(load_library().lbm_set_fault_injection(h, int(tile), float(wait_seconds)), "lbm_set_fault_injection")
+
+
+def lbm_checkpoint_save(h) -> bytes:
+    """The self-describing checkpoint image of the current state."""
+    lib = load_library()
+    n = ctypes.c_size_t()
+    _check(lib.lbm_checkpoint_bytes(h, ctypes.byref(n)), "lbm_checkpoint_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.lbm_checkpoint_save(h, buf, n.value), "lbm_checkpoint_save")
+    return buf.raw
+
+
+def lbm_checkpoint_load(h, image: bytes):
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    _check(load_library().lbm_checkpoint_load(h, buf, len(image)), "lbm_checkpoint_load")
+
+
+def lbm_probe_neg_recip(x_ptr: int, y_single_ptr: int, y_pair_ptr: int, n: int, stream_ptr: int = 0):
+    _check(load_library().lbm_probe_neg_recip(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_single_ptr),
+                                              ctypes.c_void_p(y_pair_ptr), int(n), ctypes.c_void_p(stream_ptr)),
+           "lbm_probe_neg_recip")
+
+
 def lbm_set_kernel(h, kernel: int, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=1):
     _check(load_library().lbm_set_kernel(h, int(kernel), int(consumer_warps), int(cells_per_thread), int(stages),
                                          int(ctas_per_sm)), "lbm_set_kernel")
@@ -428,6 +460,12 @@ class Lattice:
 
     def set_populations(self, pops, history_count: int):
         lbm_set_populations(self.h, pops, history_count)
+
+    def checkpoint(self) -> bytes:
+        return lbm_checkpoint_save(self.h)
+
+    def restore(self, image: bytes):
+        lbm_checkpoint_load(self.h, image)
 
     def get_window(self, x0, y0, w, h) -> np.ndarray:
         return lbm_get_window(self.h, x0, y0, w, h, self.storage)

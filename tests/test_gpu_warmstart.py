@@ -25,7 +25,11 @@ def test_warm_start_gains_over_cold_start():
     for r in rows:
         assert r["cold"]["steps"] is not None  # the judge itself reached periodic shedding
         assert r["warm"]["steps"] is not None
-        # the same converged cycle: mean drag and Strouhal number within 1 %
-        assert r["drift"]["cd_mean"] <= 0.01 and r["drift"]["st"] <= 0.01, r
+        # the acceptance rule: mean drag, lift amplitude and Strouhal number
+        # of the converged cycle each within 1 % of the cold start's
+        print(f"warm start Re {r['Re']:.1f}: drift {r['drift']}, steps {r['cold']['steps']} -> "
+              f"{r['warm']['steps']}")
+        assert all(r["drift"][k] <= 0.01 for k in ("cd_mean", "cl_amp", "st")), r
+        assert r["accepted"]
     # the gain: fewer steps to periodic shedding from the prediction
     assert np.median([r["step_speedup"] for r in rows]) > 1.0, rows
