@@ -148,6 +148,9 @@ def test_negative_reciprocal_within_one_ulp_for_every_density():
     rounded = exact.astype(np.float32)
     ulp = np.spacing(np.abs(rounded)).astype(np.float64)
     err = np.abs(y1.astype(np.float64) - exact) / ulp
+    exact_share = float(np.mean(y1 == rounded))
+    print(f"-1/x on {x.size} floats in [0.5, 1.5]: max error {err.max():.4f} ulp, "
+          f"correctly rounded {100 * exact_share:.3f} %")
     assert err.max() < 1.0, err.max()
     # and nearly always the correctly rounded quotient
-    assert np.mean(y1 == rounded) > 0.99
+    assert exact_share > 0.99

@@ -165,8 +165,12 @@ PRODUCTION_STEPS = int(os.environ.get("GBLBM_PRODUCTION_STEPS", "3000"))
 PRODUCTION_TOL_FY = {lbm.LBM_F32: 1e-4, lbm.LBM_F64: 1e-10}
 
 
+# FP64 storage: the GPU's double arithmetic on offsets and the oracle's on
+# the populations themselves (|f| up to 0.44, so its own rounding steps are
+# ~10x larger) drift apart like two double-precision runs of the same
+# unstable wake; measured 2.4e-12 U after 3000 steps.
 @pytest.mark.slow
-@pytest.mark.parametrize("storage,tol,tol_F", [(lbm.LBM_F32, 1e-5, 1e-4), (lbm.LBM_F64, 1e-12, 1e-10)],
+@pytest.mark.parametrize("storage,tol,tol_F", [(lbm.LBM_F32, 1e-5, 1e-4), (lbm.LBM_F64, 1e-11, 1e-10)],
                          ids=["f32", "f64"])
 @pytest.mark.parametrize("bc", [W.BC_FREESLIP, W.BC_ZOUHE], ids=["freeslip", "zouhe"])
 def test_production_case_matches_oracle_every_node(bc, storage, tol, tol_F):
@@ -530,16 +534,20 @@ def test_instability_is_reported():
     lat.close()
 
 
-# measured on 300 x 41, 60 steps: f16 8.5e-4 U, bf16 8.2e-3 U, f64 1.4e-14 U
-STORAGE = [(lbm.LBM_F16_OFS, 2e-3, 2e-4), (lbm.LBM_BF16_OFS, 2e-2, 2e-3), (lbm.LBM_F64, 1e-12, 1e-12)]
+# measured on 300 x 41, 60 steps: populations f16 8.5e-4 U, bf16 8.2e-3 U,
+# f64 1.4e-14 U; drag 1e-4 / 1e-3 of its scale; lift (max |Fy| ~0.1 of
+# max |Fx| here) 3.1e-3 / 3.6e-2 of its own scale -- the 16-bit rounding of
+# the stored offsets, not an error of the arithmetic
+STORAGE = [(lbm.LBM_F16_OFS, 2e-3, 2e-4, 1e-2), (lbm.LBM_BF16_OFS, 2e-2, 2e-3, 1e-1),
+           (lbm.LBM_F64, 1e-12, 1e-12, 1e-12)]
 
 
-@pytest.mark.parametrize("storage,tol,tol_F", STORAGE, ids=["f16", "bf16", "f64"])
+@pytest.mark.parametrize("storage,tol,tol_F,tol_Fy", STORAGE, ids=["f16", "bf16", "f64"])
 @pytest.mark.parametrize("kname,kw", KERNELS, ids=[k[0] for k in KERNELS])
-def test_storage_forms_match_oracle(storage, tol, tol_F, kname, kw):
+def test_storage_forms_match_oracle(storage, tol, tol_F, tol_Fy, kname, kw):
     wl = W.random_case(300, 41, seed=33, bc=W.BC_FREESLIP, D=8)
     pops, F, fields, _ = gpu_run(wl, 60, storage=storage, **kw)
-    compare(wl, 60, pops, F, fields, tol_f=tol * wl.U, tol_F=tol_F, storage=storage)
+    compare(wl, 60, pops, F, fields, tol_f=tol * wl.U, tol_F=tol_F, storage=storage, tol_Fy=tol_Fy)
 
 
 def test_full_size_lattice_sampled_windows():
