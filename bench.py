@@ -73,6 +73,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed on its own."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -544,6 +555,83 @@ def run_warmstart(args):
     return 0
 
 
+def run_network(args):
+    """The warm-start network's convolutions at the training shape (N = 4
+    samples of 800 x 1600, D = 40): per layer, the forward, input-gradient
+    and weight-gradient calls timed with CUDA events on their stream, as
+    TFLOP/s against the dense BF16 peak, for the tensor-core (tcgen05) and
+    the mma.sync kernels; and one whole training iteration."""
+    import numpy as np
+    import torch
+    from paper_2605_02185_gb300 import nn
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    N, H, W = args.net_batch, 800, 1600
+    peak, src = measured_bf16_peak()
+    net = nn.WarmStartNet(N, H, W, device, seed=0)
+    rng = np.random.default_rng(0)
+    with torch.no_grad():
+        net.x0.copy_(torch.from_numpy(rng.standard_normal(net.x0.shape).astype(np.float32)).to(torch.bfloat16))
+    stream = torch.cuda.current_stream(device)
+    dims = {"c1": 0, "d1": 0, "he": 0, "c2": 1, "d2": 1, "c3": 2, "d3": 2, "c4": 3}
+    rows = []
+    reps = max(3, args.steps // 4)
+    for name, c in net.layers.items():
+        h, w = net.dims[dims[name[:2]]]
+        flops = 2.0 * N * h * w * 9 * c.cin * c.cout
+        x = torch.from_numpy(rng.standard_normal((N, h, w, c.cin)).astype(np.float32)).to(device, torch.bfloat16)
+        gy = torch.from_numpy(rng.standard_normal((N, h, w, c.cout)).astype(np.float32)).to(device, torch.bfloat16)
+        y = torch.empty((N, h, w, c.cout), dtype=torch.bfloat16, device=device)
+        gx = torch.empty((N, h, w, c.cin), dtype=torch.bfloat16, device=device)
+        row = {"layer": name, "H": h, "W": w, "cin": c.cin, "cout": c.cout, "gflop": flops / 1e9}
+        calls = {
+            "fwd": lambda: nn.conv3x3_fwd(x, c.cin, c.w16, c.b, y, c.cout, N, h, w, c.cin, c.cout, 1),
+            "dgrad": lambda: nn.conv3x3_dgrad(gy, c.cout, c.wf16, gx, c.cin, N, h, w, c.cin, c.cout),
+            "wgrad": lambda: nn.conv3x3_wgrad(x, c.cin, gy, c.cout, c.gw, c.gb, N, h, w, c.cin, c.cout),
+        }
+        for impl_name, impl in (("tcgen05", nn.IMPL_AUTO), ("mma_sync", nn.IMPL_MMA_SYNC)):
+            nn.set_conv_impl(impl)
+            for kind, fn in calls.items():
+                for _ in range(2):
+                    fn()
+                dt = time_steps(lambda k: [fn() for _ in range(k)], reps, stream) / reps
+                row[f"{kind}_{impl_name}_tflops"] = flops / dt / 1e12
+        nn.set_conv_impl(nn.IMPL_AUTO)
+        rows.append(row)
+        del x, gy, y, gx
+    # one training iteration: forward, loss, backward, Adam
+    tg = torch.zeros((N * H * W, 3), dtype=torch.float32, device=device)
+    wg = torch.ones(N * H * W, dtype=torch.float32, device=device)
+
+    def iteration(k):
+        for _ in range(k):
+            net.forward()
+            net.loss_and_grad(tg, wg)
+            net.backward()
+            net.adam_step(1e-4)
+
+    iters = {}
+    for impl_name, impl in (("tcgen05", nn.IMPL_AUTO), ("mma_sync", nn.IMPL_MMA_SYNC)):
+        nn.set_conv_impl(impl)
+        iteration(2)
+        iters[impl_name] = time_steps(iteration, reps, stream) / reps
+    nn.set_conv_impl(nn.IMPL_AUTO)
+    assert nn.status(reset=True) == 0
+    fl = 3 * net.flops_per_sample() * N
+    print(json.dumps({
+        "metric": "warm-start network training iteration (3x3 conv fwd + both gradients), BF16 tensor cores",
+        "value": fl / iters["tcgen05"] / 1e12, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1,
+        "data": "synthetic", "dtype": "bf16 (FP32 accumulation)",
+        "config": {"workload": f"warm-start U-Net, N = {N}, {H} x {W}", "reps": reps},
+        "iteration_ms": {k: v * 1e3 for k, v in iters.items()},
+        "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "peak_source": src,
+                     "frac": fl / iters["tcgen05"] / 1e12 / peak},
+        "layers": rows}), flush=True)
+    return 0
+
+
 def run_statistics(args):
     """Physics of the production case (Re = 100, D = 80, 3200 x 1600, U = 0.05,
     tau = 0.62, or the case --D/--U/--Re give): each (top/bottom rule,
@@ -628,7 +716,8 @@ def main(argv=None):
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="0: the library's tuned default")
     ap.add_argument("--workload", default="throughput",
-                    choices=["throughput", "production", "parity", "batch", "warmstart", "statistics"])
+                    choices=["throughput", "production", "parity", "batch", "warmstart", "statistics", "network"])
+    ap.add_argument("--net-batch", type=int, default=4, help="network workload: samples per batch")
     ap.add_argument("--runs", default="freeslip:f64,freeslip:f32,freeslip:f16,freeslip:bf16,periodic:f32,"
                                       "zouhe:f32,movingwall:f32",
                     help="statistics workload: comma list of top/bottom rule:storage")
@@ -658,6 +747,8 @@ def main(argv=None):
         return run_warmstart(args)
     if args.workload == "statistics":
         return run_statistics(args)
+    if args.workload == "network":
+        return run_network(args)
     wl = {"throughput": W.THROUGHPUT_D400, "production": W.PRODUCTION_D80, "parity": W.PARITY_D10}[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

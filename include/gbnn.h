@@ -24,6 +24,30 @@
 extern "C" {
 #endif
 
+/* ---- implementation choice ------------------------------------------------
+ * GBNN_IMPL_TCGEN05: the Blackwell tensor-core kernels -- tcgen05.mma with the
+ *   accumulator in tensor memory, operands staged by the TMA engine into a
+ *   multi-stage shared-memory ring.  The forward (and input-gradient) call
+ *   takes them when cin (the convolution's input channels) and cout are
+ *   multiples of 32 (cout <= 256, or two equal halves of a multiple of 32 up
+ *   to 512), both channel strides are multiples of 8 and x, w, y (and mask)
+ *   are 16-byte aligned; the weight-gradient call when cin and cout are
+ *   multiples of 32, cout <= 256, strides multiples of 8, x and gy 16-byte
+ *   aligned.
+ * GBNN_IMPL_MMA_SYNC: the warp-level m16n8k16 kernels (every shape).
+ * GBNN_IMPL_AUTO (default): tcgen05 where the shape is taken, else mma.sync.
+ * gbnn_set_conv_impl applies to every later convolution call of the process
+ * (not thread-safe); with GBNN_IMPL_TCGEN05 a shape it does not take returns
+ * -1.  gbnn_status reads (and with reset != 0 clears) the device status word
+ * of the tensor-core kernels: 1 if one of their bounded waits (2 s) gave up,
+ * 0 otherwise, -2 on a CUDA error; it synchronises with the device. */
+#define GBNN_IMPL_AUTO 0
+#define GBNN_IMPL_MMA_SYNC 1
+#define GBNN_IMPL_TCGEN05 2
+int gbnn_set_conv_impl(int impl);
+int gbnn_conv_impl(void);
+int gbnn_status(int reset);
+
 /* y = act(conv3x3(x, w) + bias), zero padding 1.  cin, x_cstride: multiples
  * of 8; cout, y_cstride even.  bias may be NULL.  relu != 0 applies ReLU.
  * If mask is not NULL the result is zeroed where mask (same pixel and

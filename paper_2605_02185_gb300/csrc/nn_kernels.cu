@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "../../include/gbnn.h"
+#include "nn_tc.h"
 
 namespace {
 
@@ -509,6 +510,8 @@ __global__ void decode_output_kernel(const bf16 *__restrict__ out, int os, const
   }
 }
 
+int g_conv_impl = GBNN_IMPL_AUTO;
+
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 65535 * 16 ? 65535 * 16 : b));
@@ -520,6 +523,16 @@ int err(cudaError_t e) { return e == cudaSuccess ? 0 : -2; }
 
 extern "C" {
 
+int gbnn_set_conv_impl(int impl) {
+  if (impl < GBNN_IMPL_AUTO || impl > GBNN_IMPL_TCGEN05) return -1;
+  g_conv_impl = impl;
+  return 0;
+}
+
+int gbnn_conv_impl(void) { return g_conv_impl; }
+
+int gbnn_status(int reset) { return gbnn_tc::status(reset); }
+
 int gbnn_conv3x3_fwd(const void *x, int x_cstride, const void *w, const float *bias, void *y, int y_cstride,
                      const void *mask, int mask_cstride, int N, int H, int W, int cin, int cout, int relu, void *stream) {
   if (!x || !w || !y || N <= 0 || H <= 0 || W <= 0 || cin <= 0 || cout <= 0) return -1;
@@ -527,6 +540,12 @@ int gbnn_conv3x3_fwd(const void *x, int x_cstride, const void *w, const float *b
   if (mask && (mask_cstride % 2 || mask_cstride < cout)) return -1;
   if ((uintptr_t)x % 16 || (uintptr_t)w % 16) return -1;
   const cudaStream_t st = (cudaStream_t)stream;
+  if (g_conv_impl != GBNN_IMPL_MMA_SYNC) {
+    const int rc = gbnn_tc::conv_fwd(x, x_cstride, w, bias, y, y_cstride, mask, mask_cstride, N, H, W, cin, cout, relu,
+                                     st);
+    if (rc != gbnn_tc::kNotEligible) return rc;
+    if (g_conv_impl == GBNN_IMPL_TCGEN05) return -1;  // required, but this shape is not taken
+  }
   const int bn = cout <= 16 ? 16 : (cout <= 32 ? 32 : 64);
   const int nch = (cout + bn - 1) / bn;
   dim3 grid((W + FW_BM - 1) / FW_BM, H, N * nch);
@@ -568,6 +587,11 @@ int gbnn_conv3x3_wgrad(const void *x, int x_cstride, const void *gy, int gy_cstr
   if (!x || !gy || !gw || N <= 0 || H <= 0 || W <= 0 || cin % 8 || cout % 8 || x_cstride % 8 || gy_cstride % 8)
     return -1;
   const cudaStream_t st = (cudaStream_t)stream;
+  if (g_conv_impl != GBNN_IMPL_MMA_SYNC) {
+    const int rc = gbnn_tc::conv_wgrad(x, x_cstride, gy, gy_cstride, gw, gb, N, H, W, cin, cout, splits, st);
+    if (rc != gbnn_tc::kNotEligible) return rc;
+    if (g_conv_impl == GBNN_IMPL_TCGEN05) return -1;
+  }
   const long long P = (long long)N * H * W;
   if (cout <= 32) {  // wide, shallow layer: all nine taps per block
     const long long nsegs = (long long)N * H * ((W + W9_PX - 1) / W9_PX);

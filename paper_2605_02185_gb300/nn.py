@@ -38,11 +38,15 @@ def _lib():
             "gbnn_encode_target": [vp, vp, vp, vp, ll, f, f, f, vp, vp, vp],
             "gbnn_decode_output": [vp, i, vp, ll, f, f, f, vp, vp, vp, vp],
             "gbnn_fill_zero": [vp, sz, vp],
+            "gbnn_set_conv_impl": [i],
+            "gbnn_status": [i],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.restype = ctypes.c_int
             fn.argtypes = args
+        lib.gbnn_conv_impl.restype = ctypes.c_int
+        lib.gbnn_conv_impl.argtypes = []
         _sig_done = True
     return lib
 
@@ -63,6 +67,27 @@ def _s(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+IMPL_AUTO, IMPL_MMA_SYNC, IMPL_TCGEN05 = 0, 1, 2
+
+
+def set_conv_impl(impl: int):
+    """Convolution kernels for later calls: IMPL_AUTO (tcgen05 where the
+    shape is taken, else mma.sync), IMPL_MMA_SYNC or IMPL_TCGEN05 (required)."""
+    _ck(_lib().gbnn_set_conv_impl(int(impl)), "gbnn_set_conv_impl")
+
+
+def conv_impl() -> int:
+    return int(_lib().gbnn_conv_impl())
+
+
+def status(reset: bool = False) -> int:
+    """Device status of the tensor-core kernels: 1 if a bounded wait gave up."""
+    rc = _lib().gbnn_status(int(reset))
+    if rc < 0:
+        raise RuntimeError(f"gbnn_status failed ({rc})")
+    return rc
 
 
 def conv3x3_fwd(x, xs, w, bias, y, ys, N, H, W, cin, cout, relu, mask=None, ms=0, stream=None):
