@@ -463,6 +463,8 @@ def run_batch(args):
     tuned = None
     if args.tune:
         tuned = autotune.tune(b, [(w.nx, w.ny) for w in cases], lbm.LBM_F32, stream, steps=10, warmup=3)
+        for row in tuned.get("table", []):
+            print(json.dumps(row), file=sys.stderr, flush=True)
         tuned = {k: v for k, v in tuned.items() if k != "table"}
     nodes, bytes_step = b.nodes()
     b.step(args.warmup)

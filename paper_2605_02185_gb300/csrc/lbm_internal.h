@@ -69,7 +69,11 @@ const KernelOps *ops_f64();
   X(11, 16, 1, 4)           \
   X(12, 12, 2, 4)           \
   X(13, 16, 2, 2)           \
-  X(14, 4, 2, 3)
+  X(14, 4, 2, 3)            \
+  X(15, 10, 2, 4)           \
+  X(16, 13, 1, 6)           \
+  X(17, 13, 1, 4)           \
+  X(18, 10, 1, 6)
 
 // Shapes of the TMA-load + TMA-bulk-store kernel X(id, warps, cells/thread, stages).
 #define GBLBM_TMA_BULK_SHAPES(X) \
