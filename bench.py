@@ -546,13 +546,15 @@ def run_warmstart(args):
                                 log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
     if rank == 0:
         print(json.dumps({
-            "metric": "wall time to periodic Cd/Cl/St, learned warm start vs cold start", "unit": "x faster",
-            "value": summary["median_time_speedup"], "higher_is_better": True, "n_gpus": 1,
+            "metric": "wall time to periodic Cd/Cl/St, learned warm start vs cold start (median over all judged "
+                      "cases; a rejected prediction costs its warm run plus the cold run)", "unit": "x faster",
+            "value": summary["median_gain_all_judged"], "higher_is_better": True, "n_gpus": 1,
             "data": "synthetic", "dtype": "bf16 network, f32 lattice",
             "config": {"workload": f"cylinder D = {cfg.D}, {40 * cfg.D} x {20 * cfg.D}, U = {cfg.U}, "
                                    f"Re in [{cfg.re_lo}, {cfg.re_hi}], MRT collision", "train_cases": cfg.train_cases,
                        "snapshots": info["snapshots"], "batch": cfg.batch},
             "summary": summary, "train": {k: v for k, v in info.items() if k != "losses"},
+            "training_cost_s": info["spinup_s"] + info["fill_s"] + info["train_s"],
             "loss_first_last": [info["losses"][0], info["losses"][-1]], "cases": rows}), flush=True)
     return 0
 

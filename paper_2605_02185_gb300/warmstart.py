@@ -345,6 +345,8 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
                                               cfg.stat_periods)
     lat.sync()
     out["warm"] = {"steps": n_warm, "wall_s": t_warm, "inference_s": t_inf, **(st_warm or {})}
+    if t_warm is None:
+        out["warm"]["limit_s"] = time.perf_counter() - t0  # ran to the step limit without becoming periodic
     lat.close()
     out["cold_periodic"] = st_cold is not None
     if st_cold and st_warm:
@@ -373,13 +375,20 @@ def evaluate(net, cfg: Config, n_eval: int = 16, device=None, log=print):
         rows.append(r)
     acc = [r for r in rows if r["accepted"]]
     judged = [r for r in rows if r["cold_periodic"]]
-    # time with the warm start as the first try: a rejected or never-periodic
-    # warm run costs its own time and then the cold run's
-    cost = [r["warm"]["wall_s"] if r["accepted"] else (r["warm"]["wall_s"] or 0.0) + r["cold"]["wall_s"] for r in judged]
+    # Time with the warm start as the first try, over every judged case: a
+    # rejected or never-periodic warm run costs its own time (up to the step
+    # limit) and then the cold run's, so the gain of a case is
+    # cold time / (warm time if accepted, else warm time + cold time).
+    for r in judged:
+        warm_t = r["warm"]["wall_s"] if r["warm"]["wall_s"] is not None else r["warm"].get("limit_s", 0.0)
+        r["cost_s"] = warm_t if r["accepted"] else warm_t + r["cold"]["wall_s"]
+        r["gain"] = r["cold"]["wall_s"] / r["cost_s"]
     summary = {
         "cases": len(rows), "cold_periodic": len(judged), "accepted": len(acc),
-        "median_step_speedup": float(np.median([r["step_speedup"] for r in acc])) if acc else None,
-        "median_time_speedup": float(np.median([r["time_speedup"] for r in acc])) if acc else None,
-        "total_time_speedup": (sum(r["cold"]["wall_s"] for r in judged) / sum(cost)) if judged else None,
+        "median_gain_all_judged": float(np.median([r["gain"] for r in judged])) if judged else None,
+        "total_time_speedup": (sum(r["cold"]["wall_s"] for r in judged) / sum(r["cost_s"] for r in judged))
+        if judged else None,
+        "median_step_speedup_accepted": float(np.median([r["step_speedup"] for r in acc])) if acc else None,
+        "median_time_speedup_accepted": float(np.median([r["time_speedup"] for r in acc])) if acc else None,
     }
     return rows, summary
