@@ -162,46 +162,67 @@ template <int BN> struct TmemCols {
   static constexpr uint32_t value = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 };
 
+// Resident CTAs per SM whose tensor-memory allocations fit in the SM's 512
+// columns, and the dynamic shared memory that keeps any more from being
+// placed there (a CTA that cannot allocate would wait for another to free).
+__host__ __device__ constexpr int tmem_ctas(uint32_t ncols) { return (int)(512u / ncols); }
+__host__ __device__ constexpr int smem_floor(uint32_t ncols) { return 233472 / (tmem_ctas(ncols) + 1) + 1024; }
+
 template <int BN, int CK, int STAGES>
 struct TcLayout {
+  static constexpr uint32_t ACC_COLS = TmemCols<BN>::value;  // one accumulator
+  static constexpr uint32_t NCOLS = 2 * ACC_COLS;            // two, double-buffered
   static constexpr int A_BYTES = kTileM * CK * 2;
   static constexpr int B_BYTES = BN * CK * 2;
   static constexpr int A_OFF = 0;
   static constexpr int B_OFF = STAGES * A_BYTES;
-  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;  // full[S], empty[S], acc, drain
-  static constexpr int BYTES = BAR_OFF + (2 * STAGES + 2) * 8 + 16;
-  static constexpr int ALLOC = BYTES + 1024;  // room to align the base to 1024 B
+  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
+  static constexpr int NBARS = 2 * STAGES + 5;
+  static constexpr int BYTES = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int ALLOC = BYTES + 1024 > smem_floor(NCOLS) ? BYTES + 1024 : smem_floor(NCOLS);
   static constexpr uint32_t SBO = 8 * CK * 2;
   static constexpr uint32_t SWZ = CK == 64 ? 2u : 4u;  // 128-byte or 64-byte swizzle
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: each CTA walks output tiles t = blockIdx.x, += gridDim.x, in
+// the order (image, row, 128-pixel segment, channel chunk) so that tiles
+// running at the same time share their input rows in L2.  The producer and
+// the MMA issuer stream k-blocks across tile boundaries; the accumulator is
+// double-buffered in tensor memory, so the epilogue of one tile overlaps the
+// main loop of the next.
 template <int BN, int CK, int STAGES>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant__ CUtensorMap tmap_w,
                    const float *__restrict__ bias, bf16 *__restrict__ y, int ys, const bf16 *__restrict__ mask, int ms,
-                   int H, int W, int cin, int nchunks, int relu) {
+                   int H, int W, int cin, int nchunks, int relu, int ntiles) {
   using Lay = TcLayout<BN, CK, STAGES>;
-  constexpr uint32_t NCOLS = TmemCols<BN>::value;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lay::BAR_OFF);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lay::BAR_OFF + (2 * STAGES + 2) * 8);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lay::BAR_OFF + Lay::NBARS * 8);
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w0 = blockIdx.x * kTileM, h = blockIdx.y;
-  const int n = blockIdx.z / nchunks, o0 = (blockIdx.z % nchunks) * BN;
   const int kchunks = cin / CK, kblocks = 9 * kchunks;
+  const int wtiles = (W + kTileM - 1) / kTileM;
   const uint32_t full0 = saddr(&bars[0]), empty0 = saddr(&bars[STAGES]);
-  const uint32_t acc_bar = saddr(&bars[2 * STAGES]), drain_bar = saddr(&bars[2 * STAGES + 1]);
+  const uint32_t accf0 = saddr(&bars[2 * STAGES]), acce0 = saddr(&bars[2 * STAGES + 2]);
+  const uint32_t drain_bar = saddr(&bars[2 * STAGES + 4]);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);   // the MMA issuer's commit
+      mbar_init(acce0 + 8 * b, 4);   // one arrival per epilogue warp
+    }
     mbar_init(drain_bar, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     prefetch_map(&tmap_w);
   }
   if (warp == 0) {
-    tmem_alloc(saddr(tmem_slot), NCOLS);
+    tmem_alloc(saddr(tmem_slot), Lay::NCOLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -219,23 +240,39 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------- TMA producer
-      int kb = 0;
-      for (; kb < kblocks; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ((kb / STAGES) - 1) & 1, s_abort)) {
-          if (!*s_abort) give_up(s_abort);
-          break;
+      int g = 0;  // k-blocks issued by this CTA
+      bool stop = false;
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const int chunk = t % nchunks, r1 = t / nchunks;
+        const int wt = r1 % wtiles, r2 = r1 / wtiles;
+        const int h = r2 % H, n = r2 / H;
+        const int w0 = wt * kTileM, o0 = chunk * BN;
+        int tap = 0, c0 = 0;
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1, s_abort)) {
+            if (!*s_abort) give_up(s_abort);
+            stop = true;
+            break;
+          }
+          if (*s_abort) {
+            stop = true;
+            break;
+          }
+          const int dy = tap / 3, dx = tap - 3 * dy;
+          mbar_expect_tx(full0 + 8 * s, (uint32_t)(Lay::A_BYTES + Lay::B_BYTES));
+          tma_load_4d(saddr(smem + Lay::A_OFF + s * Lay::A_BYTES), &tmap_x, full0 + 8 * s, c0, w0 + dx - 1,
+                      h + dy - 1, n);
+          tma_load_2d(saddr(smem + Lay::B_OFF + s * Lay::B_BYTES), &tmap_w, full0 + 8 * s, tap * cin + c0, o0);
+          c0 += CK;
+          if (c0 == cin) {
+            c0 = 0;
+            ++tap;
+          }
         }
-        if (*s_abort) break;
-        const int tap = kb / kchunks, c0 = (kb - tap * kchunks) * CK;
-        const int dy = tap / 3, dx = tap - 3 * dy;
-        mbar_expect_tx(full0 + 8 * s, (uint32_t)(Lay::A_BYTES + Lay::B_BYTES));
-        tma_load_4d(saddr(smem + Lay::A_OFF + s * Lay::A_BYTES), &tmap_x, full0 + 8 * s, c0, w0 + dx - 1, h + dy - 1,
-                    n);
-        tma_load_2d(saddr(smem + Lay::B_OFF + s * Lay::B_BYTES), &tmap_w, full0 + 8 * s, tap * cin + c0, o0);
       }
       // leave no copy in flight into this CTA's shared memory
-      for (int q = kb - STAGES < 0 ? 0 : kb - STAGES; q < kb; ++q) {
+      for (int q = g - STAGES < 0 ? 0 : g - STAGES; q < g; ++q) {
         const unsigned long long t0 = now_ns();
         while (!mbar_test(full0 + 8 * (q % STAGES), (q / STAGES) & 1)) {
           if (now_ns() - t0 > kWaitNs) {
@@ -248,57 +285,75 @@ __global__ void __launch_bounds__(kThreads, 2)
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BN);
-      int issued = 0;
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, s_abort)) {
+      int g = 0, i = 0, issued = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !mbar_wait(acce0 + 8 * b, ((i >> 1) - 1) & 1, s_abort)) {  // epilogue done with buffer b
           if (!*s_abort) give_up(s_abort);
           break;
         }
         tc_fence_after();
-        const uint32_t a = saddr(smem + Lay::A_OFF + s * Lay::A_BYTES);
-        const uint32_t b = saddr(smem + Lay::B_OFF + s * Lay::B_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(b * Lay::ACC_COLS);
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait(full0 + 8 * s, (g / STAGES) & 1, s_abort)) {
+            if (!*s_abort) give_up(s_abort);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = saddr(smem + Lay::A_OFF + s * Lay::A_BYTES);
+          const uint32_t bb = saddr(smem + Lay::B_OFF + s * Lay::B_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < CK / 16; ++kk)  // K = 16 per MMA: 32 bytes further along the swizzled row
-          umma_bf16(tmem, kmajor_desc(a + 32 * kk, Lay::SBO, Lay::SWZ), kmajor_desc(b + 32 * kk, Lay::SBO, Lay::SWZ),
-                    idesc, (kb | kk) != 0);
-        umma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
-        ++issued;
+          for (int kk = 0; kk < CK / 16; ++kk)  // K = 16 per MMA: 32 bytes further along the swizzled row
+            umma_bf16(acc, kmajor_desc(a + 32 * kk, Lay::SBO, Lay::SWZ),
+                      kmajor_desc(bb + 32 * kk, Lay::SBO, Lay::SWZ), idesc, (kb | kk) != 0);
+          umma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
+          ++issued;
+        }
+        if (!stop) umma_commit(accf0 + 8 * b);  // accumulator b is complete
       }
-      if (issued == kblocks) {
-        umma_commit(acc_bar);  // the accumulator is complete
-      } else if (issued > 0) {
-        // stopped early: wait (bounded) until the MMAs in flight are done
+      if (issued > 0) {  // every MMA done before the tensor memory is freed
         umma_commit(drain_bar);
         const unsigned long long t0 = now_ns();
         while (!mbar_test(drain_bar, 0)) {
-          if (now_ns() - t0 > kWaitNs) break;
+          if (now_ns() - t0 > kWaitNs) {
+            give_up(s_abort);
+            break;
+          }
         }
       }
     }
   } else {  // ---------------- epilogue warps 2..5
     const int quarter = warp & 3;  // tensor-memory lanes 32 * quarter .. + 31
     const int m = 32 * quarter + lane;
-    const int px = w0 + m;
-    bool ok = mbar_wait(acc_bar, 0, s_abort);
-    if (!ok && !*s_abort) give_up(s_abort);
-    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective: one decision per warp
-    if (ok) {
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1;
+      bool ok = mbar_wait(accf0 + 8 * b, (i >> 1) & 1, s_abort);
+      if (!ok && !*s_abort) give_up(s_abort);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective: one decision per warp
+      if (!ok) break;
       tc_fence_after();
+      const int chunk = t % nchunks, r1 = t / nchunks;
+      const int wt = r1 % wtiles, r2 = r1 / wtiles;
+      const int h = r2 % H, n = r2 / H;
+      const int px = wt * kTileM + m, o0 = chunk * BN;
       const size_t pix = ((size_t)n * H + h) * W + px;
 #pragma unroll 1
       for (int j0 = 0; j0 < BN; j0 += 32) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0, r);
+        tmem_ld32(tmem + (uint32_t)(b * Lay::ACC_COLS) + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0, r);
         tmem_ld_wait();
         if (px < W) {
           const int o = o0 + j0;
           float v[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]) + (bias ? __ldg(bias + o + i) : 0.f);
+          for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]) + (bias ? __ldg(bias + o + q) : 0.f);
           if (relu) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+            for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
           }
           if (mask) {
             const uint4 *mp = reinterpret_cast<const uint4 *>(mask + pix * ms + o);
@@ -327,13 +382,17 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         }
       }
+      // accumulator b may be overwritten once all four warps have read it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, NCOLS);
+    tmem_dealloc(tmem, Lay::NCOLS);
   }
 }
 
@@ -394,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int *s_abort = &s_abort_store;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mtile = blockIdx.y;
-  const long long k0 = (long long)blockIdx.x * ksteps_per_cta;
+  const int mtile = blockIdx.x;  // M tiles of one K range run side by side and share their loads in L2
+  const long long k0 = (long long)blockIdx.y * ksteps_per_cta;
   const long long k1 = k0 + ksteps_per_cta < ksteps ? k0 + ksteps_per_cta : ksteps;
   const int nk = k1 > k0 ? (int)(k1 - k0) : 0;
   const int segs = (W + kWgPix - 1) / kWgPix;  // K steps per image row
@@ -426,6 +485,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0 && nk > 0) {  // ---------------- TMA producer
+      // row block -> (tap, 32-channel chunk): the channel and the tap's shift
+      // of each of the four boxes; blocks past the last one load a box wholly
+      // outside the image (zeros)
+      int bc[4], bdx[4], bdy[4];
+      bool blive[4];
+#pragma unroll
+      for (int rb = 0; rb < 4; ++rb) {
+        const int blk = 4 * mtile + rb;
+        const int tap = blk / cchunks, dy = tap / 3;
+        blive[rb] = blk < nblocks;
+        bc[rb] = blive[rb] ? (blk - tap * cchunks) * 32 : 0;
+        bdx[rb] = tap - 3 * dy - 1;
+        bdy[rb] = dy - 1;
+      }
+      // the K step's image row and segment, advanced incrementally
+      int seg = (int)(k0 % segs);
+      const long long row0 = k0 / segs;
+      int h = (int)(row0 % H), n = (int)(row0 / H);
       int kb = 0;
       for (; kb < nk; ++kb) {
         const int s = kb % STAGES;
@@ -434,26 +511,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         if (*s_abort) break;
-        const long long k = k0 + kb;
-        const int w0 = (int)(k % segs) * kWgPix;
-        const long long row = k / segs;
-        const int h = (int)(row % H), n = (int)(row / H);
+        const int w0 = seg * kWgPix;
         mbar_expect_tx(full0 + 8 * s, (uint32_t)(Lay::A_BYTES + Lay::B_BYTES));
         const uint32_t a = saddr(smem + Lay::A_OFF + s * Lay::A_BYTES);
 #pragma unroll
         for (int rb = 0; rb < 4; ++rb) {
-          // row block -> (tap, chunk); blocks past the last one load a box
-          // wholly outside the image (zeros)
-          const int blk = 4 * mtile + rb;
-          const int tap = blk / cchunks, c0 = (blk - tap * cchunks) * 32;
-          const int dy = tap / 3, dx = tap - 3 * dy;
-          const bool live = blk < nblocks;
-          tma_load_4d(a + rb * kWgBlockBytes, &tmap_x, full0 + 8 * s, live ? c0 : 0, live ? w0 + dx - 1 : W,
-                      live ? h + dy - 1 : H, n);
+          tma_load_4d(a + rb * kWgBlockBytes, &tmap_x, full0 + 8 * s, bc[rb], blive[rb] ? w0 + bdx[rb] : W,
+                      blive[rb] ? h + bdy[rb] : H, n);
         }
         const uint32_t b = saddr(smem + Lay::B_OFF + s * Lay::B_BYTES);
 #pragma unroll
         for (int nb = 0; nb < BN / 32; ++nb) tma_load_4d(b + nb * kWgBlockBytes, &tmap_g, full0 + 8 * s, 32 * nb, w0, h, n);
+        if (++seg == segs) {
+          seg = 0;
+          if (++h == H) {
+            h = 0;
+            ++n;
+          }
+        }
       }
       for (int q = kb - STAGES < 0 ? 0 : kb - STAGES; q < kb; ++q) {
         const unsigned long long t0 = now_ns();
@@ -561,19 +636,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
 template <int BN, int CK, int STAGES>
 cudaError_t launch(const CUtensorMap &tx, const CUtensorMap &tw, const float *bias, bf16 *y, int ys, const bf16 *mask,
                    int ms, int N, int H, int W, int cin, int nchunks, int relu, cudaStream_t st) {
   using Lay = TcLayout<BN, CK, STAGES>;
   auto kern = conv_tc_kernel<BN, CK, STAGES>;
-  static bool prepared = false;
-  if (!prepared) {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::ALLOC);
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::ALLOC);
     if (e != cudaSuccess) return e;
-    prepared = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, Lay::ALLOC);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (per_sm > tmem_ctas(Lay::NCOLS)) per_sm = tmem_ctas(Lay::NCOLS);
   }
-  dim3 grid((W + kTileM - 1) / kTileM, H, N * nchunks);
-  kern<<<grid, kThreads, Lay::ALLOC, st>>>(tx, tw, bias, y, ys, mask, ms, H, W, cin, nchunks, relu);
+  const long long ntiles = (long long)N * H * ((W + kTileM - 1) / kTileM) * nchunks;
+  if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  const int grid = (int)(ntiles < (long long)per_sm * sm_count() ? ntiles : (long long)per_sm * sm_count());
+  kern<<<grid, kThreads, Lay::ALLOC, st>>>(tx, tw, bias, y, ys, mask, ms, H, W, cin, nchunks, relu, (int)ntiles);
   return cudaGetLastError();
 }
 
@@ -616,7 +706,6 @@ int conv_fwd(const void *x, int xs, const void *w, const float *bias, void *y, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return -2;
   }
-  if ((long long)N * nchunks > 65535 || H > 65535) return kNotEligible;
   const bf16 *mb = (const bf16 *)mask;
   bf16 *yb = (bf16 *)y;
   cudaError_t e = cudaErrorInvalidValue;
@@ -654,7 +743,7 @@ cudaError_t launch_wgrad(const CUtensorMap &tx, const CUtensorMap &tg, float *gw
   }
   const long long per = (ksteps + splits - 1) / splits;
   const int nsplit = (int)((ksteps + per - 1) / per);
-  kern<<<dim3(nsplit, mtiles), kThreads, Lay::ALLOC, st>>>(tx, tg, gw, H, W, cin, cout, nblocks, ksteps, per);
+  kern<<<dim3(mtiles, nsplit), kThreads, Lay::ALLOC, st>>>(tx, tg, gw, H, W, cin, cout, nblocks, ksteps, per);
   return cudaGetLastError();
 }
 
@@ -696,7 +785,7 @@ int conv_wgrad(const void *x, int xs, const void *gy, int gs, float *gw, float *
     const long long cap = (ksteps + 7) / 8;
     splits = (int)(want < 1 ? 1 : (want > cap ? (cap < 1 ? 1 : cap) : want));
   }
-  if (splits > 65535 * 8) splits = 65535 * 8;
+  if (splits > 65535) splits = 65535;
   cudaError_t e;
   switch (bn) {
     case 32: e = launch_wgrad<32, 8>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;

@@ -33,9 +33,13 @@ from . import workloads as W
 class Config:
     D: int = 40
     U: float = 0.05
+    # Training and held-out Re both span [re_lo, re_hi]: at U = 0.05 the cold
+    # start reaches a clean limit cycle only up to Re ~ 95 on the 40D x 20D box
+    # (above, an acoustic mode of the box modulates the lift), so that is the
+    # range where the cold start can judge a prediction.
     re_lo: float = 60.0
-    re_hi: float = 200.0
-    train_re_hi: float = 100.0  # training cases: Re in [re_lo, train_re_hi], where U = 0.05 sheds cleanly
+    re_hi: float = 95.0
+    train_re_hi: float = 95.0  # training cases: Re in [re_lo, min(train_re_hi, re_hi)]
     train_cases: int = 32
     snapshots: int = 20000    # snapshots the solver hands to the trainer
     replay: int = 1024        # snapshots held in the replay buffer (device memory)
