@@ -285,7 +285,7 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.wait_ns = 1000000000ull;  // every bounded device wait gives up after 1 s
   p.fault_tile = -1;
 
-  int shape = default_shape(o->storage);
+  int shape = default_shape(o->storage, o->nx);
   int kernel = o->kernel;
   int ctas = o->ctas_per_sm > 0 ? o->ctas_per_sm : 1;
   if (kernel == LBM_KERNEL_TMA_BULK) shape = 0;
@@ -517,7 +517,7 @@ int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int cta
   if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
-  int shape = kernel == LBM_KERNEL_TMA_BULK ? 0 : default_shape(c->o.storage);
+  int shape = kernel == LBM_KERNEL_TMA_BULK ? 0 : default_shape(c->o.storage, c->nx);
   int ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
   if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
     shape = find_shape(kernel, ncw, cpt, stages);
