@@ -178,7 +178,8 @@ struct TcLayout {
   static constexpr int B_OFF = STAGES * A_BYTES;
   static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
   static constexpr int NBARS = 2 * STAGES + 5;
-  static constexpr int BYTES = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int BIAS_OFF = BAR_OFF + NBARS * 8 + 16;  // the bias of every output channel
+  static constexpr int BYTES = BIAS_OFF + 512 * 4;
   static constexpr int ALLOC = BYTES + 1024 > smem_floor(NCOLS) ? BYTES + 1024 : smem_floor(NCOLS);
   static constexpr uint32_t SBO = 8 * CK * 2;
   static constexpr uint32_t SWZ = CK == 64 ? 2u : 4u;  // 128-byte or 64-byte swizzle
@@ -207,9 +208,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
 
+  float *sbias = reinterpret_cast<float *>(smem + Lay::BIAS_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kchunks = cin / CK, kblocks = 9 * kchunks;
   const int wtiles = (W + kTileM - 1) / kTileM;
+  for (int o = threadIdx.x; o < nchunks * BN; o += blockDim.x) sbias[o] = bias ? bias[o] : 0.f;
   const uint32_t full0 = saddr(&bars[0]), empty0 = saddr(&bars[STAGES]);
   const uint32_t accf0 = saddr(&bars[2 * STAGES]), acce0 = saddr(&bars[2 * STAGES + 2]);
   const uint32_t drain_bar = saddr(&bars[2 * STAGES + 4]);
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int o = o0 + j0;
           float v[32];
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]) + (bias ? __ldg(bias + o + q) : 0.f);
+          for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]) + sbias[o + q];
           if (relu) {
 #pragma unroll
             for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
@@ -655,10 +658,21 @@ cudaError_t launch(const CUtensorMap &tx, const CUtensorMap &tw, const float *bi
   if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::ALLOC);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, Lay::ALLOC);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > tmem_ctas(Lay::NCOLS)) per_sm = tmem_ctas(Lay::NCOLS);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per
+    // CTA), registers (64K per SM, allocated in units of 8 per thread),
+    // threads, and the tensor-memory columns
+    const int regs = (fa.numRegs + 7) / 8 * 8;
+    int n = 233472 / (Lay::ALLOC + 1024);
+    n = n < 65536 / (regs * kThreads) ? n : 65536 / (regs * kThreads);
+    n = n < 2048 / kThreads ? n : 2048 / kThreads;
+    n = n < tmem_ctas(Lay::NCOLS) ? n : tmem_ctas(Lay::NCOLS);
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    per_sm = n;
   }
   const long long ntiles = (long long)N * H * ((W + kTileM - 1) / kTileM) * nchunks;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;

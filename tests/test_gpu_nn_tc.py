@@ -144,3 +144,72 @@ def test_tc_weight_gradient_of_channel_slices():
     torch.cuda.synchronize()
     rw, _ = C.conv3x3_wgrad(f64(xb)[..., 64:], f64(gyb)[..., 128:])
     assert rel_err(gw.cpu().numpy(), rw) <= 1e-4
+
+
+# Network-sized shapes: many output tiles per persistent CTA (both
+# tensor-memory accumulators in use, k-blocks streaming across tiles) and
+# long split-K ranges.  The reference is the mma.sync kernel family, itself
+# checked against the FP64 oracle above; the two differ only in FP32
+# summation order and the last bfloat16 rounding.
+LARGE = [(2, 100, 800, 32, 32), (1, 64, 400, 96, 32), (2, 50, 400, 64, 128), (1, 100, 200, 384, 128),
+         (4, 25, 100, 128, 256), (1, 40, 1600, 192, 64)]
+
+
+def both_impls(fn):
+    outs = {}
+    for impl in (nn.IMPL_TCGEN05, nn.IMPL_MMA_SYNC):
+        nn.set_conv_impl(impl)
+        outs[impl] = fn()
+        torch.cuda.synchronize()
+    nn.set_conv_impl(nn.IMPL_AUTO)
+    return outs[nn.IMPL_TCGEN05], outs[nn.IMPL_MMA_SYNC]
+
+
+@pytest.mark.parametrize("N,H,W,cin,cout", LARGE)
+def test_tc_network_sized_shapes_match_mma_sync(N, H, W, cin, cout):
+    rng = np.random.default_rng(100 + cin + cout + W)
+    x = bf(rng.standard_normal((N, H, W, cin)))
+    w = bf(rng.standard_normal((cout, 3, 3, cin)) / np.sqrt(9 * cin))
+    b = torch.from_numpy(rng.standard_normal(cout).astype(np.float32)).to(DEV)
+    gy = bf(rng.standard_normal((N, H, W, cout)))
+    xm = bf(rng.standard_normal((N, H, W, cin)))
+    wf = torch.empty((cin, 3, 3, cout), dtype=torch.bfloat16, device=DEV)
+    nn.flip_weights(w, wf, cout, cin)
+
+    def fwd():
+        y = torch.full((N, H, W, cout), float("nan"), dtype=torch.bfloat16, device=DEV)
+        nn.conv3x3_fwd(x, cin, w, b, y, cout, N, H, W, cin, cout, 1)
+        return f64(y)
+
+    def dgrad():
+        gx = torch.full((N, H, W, cin), float("nan"), dtype=torch.bfloat16, device=DEV)
+        nn.conv3x3_dgrad(gy, cout, wf, gx, cin, N, H, W, cin, cout, mask=xm, ms=cin)
+        return f64(gx)
+
+    def wgrad():
+        gw = torch.zeros((cout, 3, 3, cin), dtype=torch.float32, device=DEV)
+        gb = torch.zeros(cout, dtype=torch.float32, device=DEV)
+        nn.conv3x3_wgrad(x, cin, gy, cout, gw, gb, N, H, W, cin, cout)
+        return np.concatenate([gw.cpu().numpy().ravel(), gb.cpu().numpy()]).astype(np.float64)
+
+    for name, fn, tol in (("fwd", fwd, 1e-2), ("dgrad", dgrad, 1e-2), ("wgrad", wgrad, 1e-4)):
+        a, ref = both_impls(fn)
+        assert rel_err(a, ref) <= tol, name
+
+
+def test_tc_whole_network_forward_matches_mma_sync():
+    """The warm-start U-Net forward at a downsized training shape (every
+    level, skip slices, ragged row tiles) with both kernel families."""
+    net = nn.WarmStartNet(2, 96, 400, DEV, seed=4)
+    rng = np.random.default_rng(8)
+    net.x0.copy_(bf(rng.standard_normal(net.x0.shape)))
+    for c in net.layers.values():  # non-trivial head weights
+        c.w.copy_(torch.from_numpy(rng.standard_normal(tuple(c.w.shape)).astype(np.float32)
+                                   * np.sqrt(2.0 / (9 * c.cin))).to(DEV))
+        c.sync_bf16(None, t=0)
+
+    def run():
+        return f64(net.forward())[..., :3]
+
+    a, ref = both_impls(run)
+    assert rel_err(a, ref) <= 3e-2
