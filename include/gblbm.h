@@ -62,6 +62,11 @@ extern "C" {
                           small offsets out of the binary16 subnormals), float arithmetic */
 #define LBM_BF16_OFS 2 /* bfloat16 offsets, float arithmetic */
 #define LBM_F64 3      /* double offsets, double arithmetic */
+#define LBM_F16_SR 4   /* as LBM_F16_OFS, but each stored value rounded stochastically: up with the
+                          probability of its distance from the grid point below (deterministic: the
+                          random bits hash the value, its node and direction), so updates smaller
+                          than the 16-bit step accumulate instead of being rounded away */
+#define LBM_BF16_SR 5  /* as LBM_BF16_OFS, rounded stochastically the same way */
 
 /* ---- collision model ---------------------------------------------------- */
 #define LBM_COLLIDE_BGK 0 /* Eq. 2: single relaxation time tau */
@@ -333,6 +338,14 @@ int lbm_batch_nodes(lbm_batch *batch, int64_t *nodes, double *bytes_per_step);
  * asynchronously on `stream` (cudaStream_t).  Lets a test bound its error
  * against the correctly rounded quotient. */
 int lbm_probe_neg_recip(const float *x, float *y_single, float *y_pair, int64_t n, void *stream);
+
+/* Diagnostic (no counterpart in the paper): the store rounding of
+ * LBM_F16_SR / LBM_BF16_SR on its own.  x: DEVICE float [n] offsets, salt:
+ * DEVICE uint32 [n] (in the kernels, a hash of node and direction), out:
+ * DEVICE uint16 [n] receiving the stored bit patterns (binary16 of 4096 x the
+ * offset, or bfloat16 of the offset), asynchronously on `stream`. */
+int lbm_probe_stochastic_round(int storage, const float *x, const uint32_t *salt, uint16_t *out, int64_t n,
+                               void *stream);
 
 const char *lbm_error_string(int code);
 const char *lbm_version(void);

@@ -101,6 +101,96 @@ template <> struct Store<double> {
   __device__ static __forceinline__ double st(C v) { return v; }
 };
 
+// ---- 16-bit storage with stochastic rounding ---------------------------------
+// Rounding to nearest loses every update smaller than half a step of the
+// 16-bit grid: where the flow changes slowly the stored offsets stop moving
+// (stagnation) and the error acts like a steady forcing that can suppress
+// vortex shedding.  These forms round up with probability equal to the
+// fraction of a step the value lies above the grid point below it, so the
+// stored value is right on average and small updates accumulate.  The
+// "random" bits are a hash of the float being rounded and of its node and
+// direction (salt), so the result is deterministic -- identical in every
+// kernel and launch shape -- and needs no random-number state: a value that
+// changes from step to step draws new bits each time.
+struct half_sr { __half v; };
+struct bf16_sr { __nv_bfloat16 v; };
+
+// The integer finaliser "lowbias32" (C. Wellons, hash-prospector, 2018).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+// Salt of population k of node (x, y).
+__device__ __forceinline__ uint32_t node_salt(int x, int y, int k) {
+  return (uint32_t)x * 0x9E3779B1u + (uint32_t)y * 0x85EBCA77u + (uint32_t)k * 0xC2B2AE3Du;
+}
+// fp32 bits with `drop` low mantissa bits to be discarded, plus a uniform
+// offset in [0, 2^drop): truncating the result rounds stochastically.
+template <int DROP>
+__device__ __forceinline__ uint32_t dither(uint32_t bits, uint32_t salt) {
+  return bits + (mix32(bits ^ salt) >> (32 - DROP));
+}
+__device__ __forceinline__ uint32_t cvt_rz_half2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+template <> struct Store<half_sr> {
+  using C = float;
+  static constexpr bool kDither = true;
+  __device__ static __forceinline__ C ld(half_sr v) { return __fmul_rn(__half2float(v.v), kHalfInv); }
+  __device__ static __forceinline__ half_sr st(C v) { return {__float2half_rn(__fmul_rn(v, kHalfScale))}; }
+  __device__ static __forceinline__ half_sr st_at(C v, uint32_t salt) {
+    const uint32_t b = dither<13>(__float_as_uint(__fmul_rn(v, kHalfScale)), salt);
+    return {__float2half_rz(__uint_as_float(b))};
+  }
+  __device__ static __forceinline__ float2 ld2(const half_sr *p) {
+    return __fmul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(p)), make_float2(kHalfInv, kHalfInv));
+  }
+  __device__ static __forceinline__ void st2_at(half_sr *p, float2 v, uint32_t salt0, uint32_t salt1) {
+    const float2 s = __fmul2_rn(v, make_float2(kHalfScale, kHalfScale));
+    const uint32_t b0 = dither<13>(__float_as_uint(s.x), salt0), b1 = dither<13>(__float_as_uint(s.y), salt1);
+    *reinterpret_cast<uint32_t *>(p) = cvt_rz_half2(__uint_as_float(b0), __uint_as_float(b1));
+  }
+};
+template <> struct Store<bf16_sr> {
+  using C = float;
+  static constexpr bool kDither = true;
+  __device__ static __forceinline__ C ld(bf16_sr v) { return __bfloat162float(v.v); }
+  __device__ static __forceinline__ bf16_sr st(C v) { return {__float2bfloat16_rn(v)}; }
+  __device__ static __forceinline__ bf16_sr st_at(C v, uint32_t salt) {
+    const uint32_t b = dither<16>(__float_as_uint(v), salt);
+    return {__ushort_as_bfloat16((unsigned short)(b >> 16))};
+  }
+  __device__ static __forceinline__ float2 ld2(const bf16_sr *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  }
+  __device__ static __forceinline__ void st2_at(bf16_sr *p, float2 v, uint32_t salt0, uint32_t salt1) {
+    const uint32_t b0 = dither<16>(__float_as_uint(v.x), salt0), b1 = dither<16>(__float_as_uint(v.y), salt1);
+    *reinterpret_cast<uint32_t *>(p) = (b0 >> 16) | (b1 & 0xFFFF0000u);
+  }
+};
+
+// Read-only cached load of one stored value.
+template <class S> __device__ __forceinline__ S ldg_s(const S *p) { return __ldg(p); }
+template <> __device__ __forceinline__ half_sr ldg_s(const half_sr *p) {
+  return {__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)))};
+}
+template <> __device__ __forceinline__ bf16_sr ldg_s(const bf16_sr *p) {
+  return {__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)))};
+}
+
+// Whether a storage type rounds stochastically (st_at / st2_at) or to
+// nearest (st / st2).
+template <class S> struct Dithers { static constexpr bool value = false; };
+template <> struct Dithers<half_sr> { static constexpr bool value = true; };
+template <> struct Dithers<bf16_sr> { static constexpr bool value = true; };
+
 // ---- per-step parameters (passed by value) -------------------------------
 struct StepParams {
   int nx, ny, pitch, bc;

@@ -24,6 +24,8 @@ inline const KernelOps *ops_for(int storage) {
     case LBM_F16_OFS: return ops_f16();
     case LBM_BF16_OFS: return ops_bf16();
     case LBM_F64: return ops_f64();
+    case LBM_F16_SR: return ops_f16sr();
+    case LBM_BF16_SR: return ops_bf16sr();
   }
   return nullptr;
 }
@@ -34,6 +36,8 @@ inline int elem_size(int storage) {
     case LBM_F16_OFS: return 2;
     case LBM_BF16_OFS: return 2;
     case LBM_F64: return 8;
+    case LBM_F16_SR: return 2;
+    case LBM_BF16_SR: return 2;
   }
   return 0;
 }
@@ -185,7 +189,7 @@ inline int default_shape(int storage, int nx) {
   }
   return best;
 }
-inline int default_ctas(int storage) { return (storage == LBM_F16_OFS || storage == LBM_BF16_OFS) ? 2 : 1; }
+inline int default_ctas(int storage) { return elem_size(storage) == 2 ? 2 : 1; }
 // Batches of many small lattices: shape 13 (16 compute warps, 2 cells per
 // thread, 2 stages) at 2 CTAs per SM, the autotuner's pick for 64 cases of
 // 800-2400 nodes wide (1.64x the same cases run one after another; the

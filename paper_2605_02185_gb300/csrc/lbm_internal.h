@@ -52,6 +52,8 @@ const KernelOps *ops_f32();
 const KernelOps *ops_f16();
 const KernelOps *ops_bf16();
 const KernelOps *ops_f64();
+const KernelOps *ops_f16sr();
+const KernelOps *ops_bf16sr();
 
 // TMA kernel shapes X(id, compute warps, cells per thread, stages).
 #define GBLBM_TMA_SHAPES(X) \

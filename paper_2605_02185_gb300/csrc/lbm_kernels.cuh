@@ -123,7 +123,12 @@ __device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &
                                            const typename Store<S>::C (&h)[9]) {
   S *o = B + (size_t)y * p.pitch + x;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
+  for (int k = 0; k < 9; ++k) {
+    if constexpr (Dithers<S>::value)
+      o[(size_t)k * p.plane] = Store<S>::st_at(h[k], node_salt(x, y, k));
+    else
+      o[(size_t)k * p.plane] = Store<S>::st(h[k]);
+  }
 }
 
 template <int MRT, class S, class Fetch, bool INTERP = false>
@@ -202,7 +207,12 @@ __device__ __forceinline__ void update_pair(S *__restrict__ B, const StepParams 
   bad |= !speed_ok(collide_model<MRT, LF2>(h, cf));
   S *o = B + (size_t)y * p.pitch + x;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Store<S>::st2(o + (size_t)k * p.plane, h[k].v);
+  for (int k = 0; k < 9; ++k) {
+    if constexpr (Dithers<S>::value)
+      Store<S>::st2_at(o + (size_t)k * p.plane, h[k].v, node_salt(x, y, k), node_salt(x + 1, y, k));
+    else
+      Store<S>::st2(o + (size_t)k * p.plane, h[k].v);
+  }
 }
 
 // ---- direct kernel: one CTA per row tile, loads straight from HBM -------
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(NT) step_direct(const S *__restrict__ A, S *__
   double fx = 0.0, fy = 0.0;
   bool bad = false;
   auto fetch = [&](int k, int sx, int sy) -> C {
-    return Store<S>::ld(__ldg(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
+    return Store<S>::ld(ldg_s(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
   };
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
@@ -404,7 +414,7 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
   double fx = 0.0, fy = 0.0;
   bool bad = false;
   auto fetch = [&](int k, int sx, int sy) -> C {
-    return Store<S>::ld(__ldg(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
+    return Store<S>::ld(ldg_s(A + (size_t)k * p.plane + (size_t)sy * p.pitch + sx));
   };
   for (int xw = x0 + (int)(threadIdx.x & ~31u); xw < x1; xw += NT) {
     const int x = xw + (int)(threadIdx.x & 31u);
@@ -706,7 +716,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
           for (int k = 0; k < 9; ++k) h[k] = (C)0;
         }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) out[k * W + (x - x0)] = Store<S>::st(h[k]);
+        for (int k = 0; k < 9; ++k) {
+          if constexpr (Dithers<S>::value)
+            out[k * W + (x - x0)] = Store<S>::st_at(h[k], node_salt(x, y, k));
+          else
+            out[k * W + (x - x0)] = Store<S>::st(h[k]);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));

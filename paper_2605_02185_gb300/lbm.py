@@ -23,12 +23,13 @@ LBM_OK = 0
 LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT = -1, -2, -3, -4
 LBM_ERR_OOM, LBM_ERR_RANGE, LBM_ERR_STATE = -5, -6, -7
 LBM_BC_FREESLIP, LBM_BC_PERIODIC, LBM_BC_ZOUHE, LBM_BC_MOVINGWALL = 0, 1, 2, 3
-LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64 = 0, 1, 2, 3
+LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64, LBM_F16_SR, LBM_BF16_SR = 0, 1, 2, 3, 4, 5
 LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK = 0, 1, 2, 3
 LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
 LBM_BOUNCE_HALFWAY, LBM_BOUNCE_INTERPOLATED = 0, 1
-ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8}
-ELEM_NUMPY = {LBM_F32: np.float32, LBM_F16_OFS: np.float16, LBM_BF16_OFS: np.uint16, LBM_F64: np.float64}
+ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8, LBM_F16_SR: 2, LBM_BF16_SR: 2}
+ELEM_NUMPY = {LBM_F32: np.float32, LBM_F16_OFS: np.float16, LBM_BF16_OFS: np.uint16, LBM_F64: np.float64,
+              LBM_F16_SR: np.float16, LBM_BF16_SR: np.uint16}
 
 
 class LBMError(RuntimeError):
@@ -112,6 +113,7 @@ def load_library(path: str | None = None):
         "lbm_checkpoint_save": (i, [vp, vp, sz]),
         "lbm_checkpoint_load": (i, [vp, vp, sz]),
         "lbm_probe_neg_recip": (i, [vp, vp, vp, i64, vp]),
+        "lbm_probe_stochastic_round": (i, [i, vp, vp, vp, i64, vp]),
         "lbm_batch_workspace_bytes": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(sz)]),
         "lbm_batch_create": (i, [i, vp, ctypes.POINTER(lbm_opts), ctypes.POINTER(vp)]),
         "lbm_batch_destroy": (None, [vp]),
@@ -323,6 +325,12 @@ def lbm_probe_neg_recip(x_ptr: int, y_single_ptr: int, y_pair_ptr: int, n: int, 
     _check(load_library().lbm_probe_neg_recip(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_single_ptr),
                                               ctypes.c_void_p(y_pair_ptr), int(n), ctypes.c_void_p(stream_ptr)),
            "lbm_probe_neg_recip")
+
+
+def lbm_probe_stochastic_round(storage: int, x_ptr: int, salt_ptr: int, out_ptr: int, n: int, stream_ptr: int = 0):
+    _check(load_library().lbm_probe_stochastic_round(int(storage), ctypes.c_void_p(x_ptr), ctypes.c_void_p(salt_ptr),
+                                                     ctypes.c_void_p(out_ptr), int(n), ctypes.c_void_p(stream_ptr)),
+           "lbm_probe_stochastic_round")
 
 
 def lbm_set_kernel(h, kernel: int, consumer_warps=0, cells_per_thread=0, stages=0, ctas_per_sm=1):

@@ -60,16 +60,28 @@ def period_amplitudes(cl) -> np.ndarray:
     return np.array(out)
 
 
-def periodic_index(cl, amp_min: float = 0.05, tol: float = 0.005, consecutive: int = 2):
+def shedding_periods(D: float, U: float, st_lo: float = 0.08, st_hi: float = 0.4):
+    """Range of lift periods (in steps) that belong to vortex shedding: a
+    Strouhal number D / (U T) between st_lo and st_hi."""
+    return D / (st_hi * U), D / (st_lo * U)
+
+
+def periodic_index(cl, amp_min: float = 0.05, tol: float = 0.005, consecutive: int = 2, period_range=None):
     """First entry index at which shedding counts as periodic: each of the
     last `consecutive` complete periods has amplitude >= amp_min and differs
-    from the period before it by less than tol (relative).  None if never."""
+    from the period before it by less than tol (relative), and -- if
+    period_range = (T_min, T_max) is given -- lasts between T_min and T_max
+    steps (so that a short acoustic ringing of the start is not taken for
+    shedding).  None if never."""
     c = np.asarray(cl, np.float64)
     z = upward_crossings(c)
     amps = period_amplitudes(c)
+    lens = np.diff(z) if len(z) > 1 else np.zeros(0)
     run = 0
     for k in range(1, len(amps)):
         ok = amps[k] >= amp_min and amps[k - 1] >= amp_min and abs(amps[k] - amps[k - 1]) < tol * amps[k]
+        if ok and period_range is not None:
+            ok = all(period_range[0] <= lens[j] <= period_range[1] for j in (k - 1, k))
         run = run + 1 if ok else 0
         if run >= consecutive:
             return int(math.ceil(z[k + 1]))

@@ -155,7 +155,7 @@ class SnapshotSource:
             for c in range(len(self.cases)):
                 if done[c] is None:
                     _, cl = self.hist[c].update()
-                    i = postprocess.periodic_index(cl)
+                    i = postprocess.periodic_index(cl, period_range=postprocess.shedding_periods(cfg.D, cfg.U))
                     if i is not None:
                         done[c] = i
         clean = []
@@ -300,7 +300,7 @@ def run_to_periodic(lat, wl: W.Workload, max_steps: int, chunk: int, t0: float, 
         lat.step(chunk)
         steps += chunk
         cd, cl = hist.update()
-        i = postprocess.periodic_index(cl)
+        i = postprocess.periodic_index(cl, period_range=postprocess.shedding_periods(wl.D, wl.U))
         if i is not None:
             t_detect = time.perf_counter() - t0
             z = postprocess.upward_crossings(cl[:i + 1])

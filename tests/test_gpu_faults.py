@@ -154,3 +154,39 @@ def test_negative_reciprocal_within_one_ulp_for_every_density():
     assert err.max() < 1.0, err.max()
     # and nearly always the correctly rounded quotient
     assert exact_share > 0.99
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_F16_SR, lbm.LBM_BF16_SR], ids=["f16sr", "bf16sr"])
+def test_stochastic_rounding_is_unbiased_and_brackets_the_value(storage):
+    """Each stored value is one of the two 16-bit neighbours of the float
+    being stored (toward zero, or one step further out), and over many
+    salts it averages to that float."""
+    rng = np.random.default_rng(3)
+    vals = np.array([1.234567e-3, -7.654321e-5, 0.0123456, -0.0021, 3.0e-6, 0.25], np.float32)
+    n = 200_000
+    x = np.repeat(vals, n)
+    salt = rng.integers(0, 2 ** 32, x.size, dtype=np.uint64).astype(np.uint32)
+    xd, sd = torch.from_numpy(x).cuda(), torch.from_numpy(salt.view(np.int32)).cuda()
+    out = torch.empty(x.size, dtype=torch.int16, device="cuda")
+    lbm.lbm_probe_stochastic_round(storage, xd.data_ptr(), sd.data_ptr(), out.data_ptr(), x.size)
+    torch.cuda.synchronize()
+    bits = out.cpu().numpy().view(np.uint16)
+    if storage == lbm.LBM_F16_SR:  # binary16 of 4096 x the offset
+        scaled = (x * np.float32(4096)).astype(np.float32)
+        t = scaled.astype(np.float16)
+        out_of = np.abs(t.astype(np.float32)) > np.abs(scaled)
+        t[out_of] = np.nextafter(t[out_of], np.float16(0))
+        u = np.nextafter(t, np.where(scaled < 0, np.float16(-np.inf), np.float16(np.inf)).astype(np.float16))
+        got = bits.view(np.float16).astype(np.float64) / 4096.0
+        lo, hi = t.astype(np.float64) / 4096.0, u.astype(np.float64) / 4096.0
+    else:  # bfloat16: truncation toward zero, or one step further out
+        tb = x.view(np.uint32) & np.uint32(0xFFFF0000)
+        got = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        lo = tb.view(np.float32).astype(np.float64)
+        hi = (tb + np.uint32(0x10000)).view(np.float32).astype(np.float64)
+    assert np.all((got == lo) | (got == hi))
+    for j, v in enumerate(vals):
+        g = got[j * n:(j + 1) * n]
+        gap = abs(hi[j * n] - lo[j * n])
+        # the mean lands on v within 5 standard errors of a two-point draw
+        assert abs(g.mean() - float(v)) <= 5 * 0.5 * gap / np.sqrt(n), (v, g.mean(), gap)

@@ -155,14 +155,14 @@ LARGE = [(2, 100, 800, 32, 32), (1, 64, 400, 96, 32), (2, 50, 400, 64, 128), (1,
          (4, 25, 100, 128, 256), (1, 40, 1600, 192, 64)]
 
 
-def both_impls(fn):
+def both_impls(fn, first=nn.IMPL_TCGEN05):
     outs = {}
-    for impl in (nn.IMPL_TCGEN05, nn.IMPL_MMA_SYNC):
+    for impl in (first, nn.IMPL_MMA_SYNC):
         nn.set_conv_impl(impl)
         outs[impl] = fn()
         torch.cuda.synchronize()
     nn.set_conv_impl(nn.IMPL_AUTO)
-    return outs[nn.IMPL_TCGEN05], outs[nn.IMPL_MMA_SYNC]
+    return outs[first], outs[nn.IMPL_MMA_SYNC]
 
 
 @pytest.mark.parametrize("N,H,W,cin,cout", LARGE)
@@ -211,5 +211,7 @@ def test_tc_whole_network_forward_matches_mma_sync():
     def run():
         return f64(net.forward())[..., :3]
 
-    a, ref = both_impls(run)
+    # automatic choice: tcgen05 for every layer it takes (all but the first
+    # layer, 8 input channels, and the head, 8 outputs)
+    a, ref = both_impls(run, first=nn.IMPL_AUTO)
     assert rel_err(a, ref) <= 3e-2

@@ -65,9 +65,9 @@ def gpu_run(wl, steps, **kw):
 
 
 def offsets_to_f(pops, U, storage=lbm.LBM_F32):
-    if storage == lbm.LBM_BF16_OFS:
+    if storage in (lbm.LBM_BF16_OFS, lbm.LBM_BF16_SR):
         g = (pops.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
-    elif storage == lbm.LBM_F16_OFS:
+    elif storage in (lbm.LBM_F16_OFS, lbm.LBM_F16_SR):
         g = pops.astype(np.float64) / 4096.0  # IEEE half holds 2^12 x the offset
     else:
         g = pops.astype(np.float64)
@@ -319,7 +319,8 @@ def test_shedding_lift_and_statistics_match_oracle():
     assert all(v <= 0.005 for v in rel.values()), rel
 
 
-@pytest.mark.parametrize("storage", [lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS], ids=["f16", "bf16"])
+@pytest.mark.parametrize("storage", [lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS, lbm.LBM_F16_SR, lbm.LBM_BF16_SR],
+                         ids=["f16", "bf16", "f16sr", "bf16sr"])
 @pytest.mark.parametrize("mrt", [False, True], ids=["bgk", "mrt"])
 def test_paired_16bit_tma_matches_direct(storage, mrt):
     """The 16-bit TMA kernel updates plain spans two adjacent nodes at a time
@@ -544,11 +545,14 @@ def test_instability_is_reported():
 # f64 1.4e-14 U; drag 1e-4 / 1e-3 of its scale; lift (max |Fy| ~0.1 of
 # max |Fx| here) 3.1e-3 / 3.6e-2 of its own scale -- the 16-bit rounding of
 # the stored offsets, not an error of the arithmetic
+# Stochastic rounding moves a value by up to one 16-bit step instead of half
+# of one: twice the round-to-nearest tolerances.
 STORAGE = [(lbm.LBM_F16_OFS, 2e-3, 2e-4, 1e-2), (lbm.LBM_BF16_OFS, 2e-2, 2e-3, 1e-1),
-           (lbm.LBM_F64, 1e-12, 1e-12, 1e-12)]
+           (lbm.LBM_F64, 1e-12, 1e-12, 1e-12), (lbm.LBM_F16_SR, 4e-3, 4e-4, 2e-2),
+           (lbm.LBM_BF16_SR, 4e-2, 4e-3, 2e-1)]
 
 
-@pytest.mark.parametrize("storage,tol,tol_F,tol_Fy", STORAGE, ids=["f16", "bf16", "f64"])
+@pytest.mark.parametrize("storage,tol,tol_F,tol_Fy", STORAGE, ids=["f16", "bf16", "f64", "f16sr", "bf16sr"])
 @pytest.mark.parametrize("kname,kw", KERNELS, ids=[k[0] for k in KERNELS])
 def test_storage_forms_match_oracle(storage, tol, tol_F, tol_Fy, kname, kw):
     wl = W.random_case(300, 41, seed=33, bc=W.BC_FREESLIP, D=8)
@@ -601,7 +605,7 @@ def test_full_size_lattice_sampled_windows():
     lat.close()
 
 
-@pytest.mark.parametrize("storage", [lbm.LBM_F32, lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS])
+@pytest.mark.parametrize("storage", [lbm.LBM_F32, lbm.LBM_F16_OFS, lbm.LBM_BF16_OFS, lbm.LBM_F16_SR])
 def test_bulk_store_kernel_matches_direct(storage):
     """TMA loads + TMA bulk stores: the same per-node arithmetic, identical bits."""
     shapes = lbm.lbm_kernel_shapes(lbm.LBM_KERNEL_TMA_BULK)

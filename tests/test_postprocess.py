@@ -39,3 +39,16 @@ def test_limit_cycle_separates_clean_from_modulated_lift():
     assert not PP.limit_cycle(beat)
     assert not PP.limit_cycle(clean[:int(3 * T)])        # too few periods
     assert not PP.limit_cycle(0.01 * clean)              # below the amplitude floor
+
+
+def test_periodicity_ignores_periods_outside_the_shedding_range():
+    # a clean short ringing (period 60 steps) passes the amplitude test but is
+    # no shedding for D = 20, U = 0.05 (St 0.08-0.4: periods 1000-5000 steps)
+    n = np.arange(6000)
+    ring = 0.3 * np.sin(2 * math.pi * n / 60.0)
+    rng = PP.shedding_periods(20, 0.05)
+    assert abs(rng[0] - 1000) < 1e-9 and abs(rng[1] - 5000) < 1e-9
+    assert PP.periodic_index(ring) is not None
+    assert PP.periodic_index(ring, period_range=rng) is None
+    shed = 0.3 * np.sin(2 * math.pi * np.arange(20000) / 1900.0)
+    assert PP.periodic_index(shed, period_range=rng) is not None
