@@ -108,10 +108,11 @@ template <> struct Store<double> {
 // vortex shedding.  These forms round up with probability equal to the
 // fraction of a step the value lies above the grid point below it, so the
 // stored value is right on average and small updates accumulate.  The
-// "random" bits are a hash of the float being rounded and of its node and
-// direction (salt), so the result is deterministic -- identical in every
-// kernel and launch shape -- and needs no random-number state: a value that
-// changes from step to step draws new bits each time.
+// "random" bits come from a hash of the node's nine new values and its
+// position (one hash per node, then one multiply per direction), so the
+// result is deterministic -- identical in every kernel and launch shape --
+// and needs no random-number state: values that change from step to step
+// draw new bits each time.
 struct half_sr { __half v; };
 struct bf16_sr { __nv_bfloat16 v; };
 
@@ -124,15 +125,27 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   return x;
 }
-// Salt of population k of node (x, y).
-__device__ __forceinline__ uint32_t node_salt(int x, int y, int k) {
-  return (uint32_t)x * 0x9E3779B1u + (uint32_t)y * 0x85EBCA77u + (uint32_t)k * 0xC2B2AE3Du;
+// Per-node seed: the bits of the node's nine post-collision offsets folded
+// together with its position, then mixed.
+__device__ __forceinline__ uint32_t dither_seed(uint32_t fold, int x, int y) {
+  return mix32(fold ^ ((uint32_t)x * 0x9E3779B1u + (uint32_t)y * 0x85EBCA77u));
 }
-// fp32 bits with `drop` low mantissa bits to be discarded, plus a uniform
-// offset in [0, 2^drop): truncating the result rounds stochastically.
+__device__ __forceinline__ uint32_t fold9(const float (&h)[9]) {
+  uint32_t f = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f ^= __float_as_uint(h[k]);
+  return f;
+}
+// Odd multipliers spreading one seed over the nine directions.
+__device__ __forceinline__ uint32_t dir_mul(int k) {
+  return k == 0 ? 0x2545F491u : k == 1 ? 0x9E3779B9u : k == 2 ? 0x85EBCA6Bu : k == 3 ? 0xC2B2AE35u
+       : k == 4 ? 0x27D4EB2Fu : k == 5 ? 0x165667B1u : k == 6 ? 0xD3A2646Du : k == 7 ? 0xFD7046C5u : 0xB55A4F09u;
+}
+// fp32 bits whose DROP low mantissa bits will be discarded, plus a uniform
+// offset in [0, 2^DROP): truncating the result rounds stochastically.
 template <int DROP>
-__device__ __forceinline__ uint32_t dither(uint32_t bits, uint32_t salt) {
-  return bits + (mix32(bits ^ salt) >> (32 - DROP));
+__device__ __forceinline__ uint32_t dither(uint32_t bits, uint32_t seed, int k) {
+  return bits + ((seed * dir_mul(k)) >> (32 - DROP));
 }
 __device__ __forceinline__ uint32_t cvt_rz_half2(float lo, float hi) {
   uint32_t r;
@@ -142,36 +155,34 @@ __device__ __forceinline__ uint32_t cvt_rz_half2(float lo, float hi) {
 
 template <> struct Store<half_sr> {
   using C = float;
-  static constexpr bool kDither = true;
   __device__ static __forceinline__ C ld(half_sr v) { return __fmul_rn(__half2float(v.v), kHalfInv); }
   __device__ static __forceinline__ half_sr st(C v) { return {__float2half_rn(__fmul_rn(v, kHalfScale))}; }
-  __device__ static __forceinline__ half_sr st_at(C v, uint32_t salt) {
-    const uint32_t b = dither<13>(__float_as_uint(__fmul_rn(v, kHalfScale)), salt);
+  __device__ static __forceinline__ half_sr st_at(C v, uint32_t seed, int k) {
+    const uint32_t b = dither<13>(__float_as_uint(__fmul_rn(v, kHalfScale)), seed, k);
     return {__float2half_rz(__uint_as_float(b))};
   }
   __device__ static __forceinline__ float2 ld2(const half_sr *p) {
     return __fmul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(p)), make_float2(kHalfInv, kHalfInv));
   }
-  __device__ static __forceinline__ void st2_at(half_sr *p, float2 v, uint32_t salt0, uint32_t salt1) {
+  __device__ static __forceinline__ void st2_at(half_sr *p, float2 v, uint32_t seed0, uint32_t seed1, int k) {
     const float2 s = __fmul2_rn(v, make_float2(kHalfScale, kHalfScale));
-    const uint32_t b0 = dither<13>(__float_as_uint(s.x), salt0), b1 = dither<13>(__float_as_uint(s.y), salt1);
+    const uint32_t b0 = dither<13>(__float_as_uint(s.x), seed0, k), b1 = dither<13>(__float_as_uint(s.y), seed1, k);
     *reinterpret_cast<uint32_t *>(p) = cvt_rz_half2(__uint_as_float(b0), __uint_as_float(b1));
   }
 };
 template <> struct Store<bf16_sr> {
   using C = float;
-  static constexpr bool kDither = true;
   __device__ static __forceinline__ C ld(bf16_sr v) { return __bfloat162float(v.v); }
   __device__ static __forceinline__ bf16_sr st(C v) { return {__float2bfloat16_rn(v)}; }
-  __device__ static __forceinline__ bf16_sr st_at(C v, uint32_t salt) {
-    const uint32_t b = dither<16>(__float_as_uint(v), salt);
+  __device__ static __forceinline__ bf16_sr st_at(C v, uint32_t seed, int k) {
+    const uint32_t b = dither<16>(__float_as_uint(v), seed, k);
     return {__ushort_as_bfloat16((unsigned short)(b >> 16))};
   }
   __device__ static __forceinline__ float2 ld2(const bf16_sr *p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
   }
-  __device__ static __forceinline__ void st2_at(bf16_sr *p, float2 v, uint32_t salt0, uint32_t salt1) {
-    const uint32_t b0 = dither<16>(__float_as_uint(v.x), salt0), b1 = dither<16>(__float_as_uint(v.y), salt1);
+  __device__ static __forceinline__ void st2_at(bf16_sr *p, float2 v, uint32_t seed0, uint32_t seed1, int k) {
+    const uint32_t b0 = dither<16>(__float_as_uint(v.x), seed0, k), b1 = dither<16>(__float_as_uint(v.y), seed1, k);
     *reinterpret_cast<uint32_t *>(p) = (b0 >> 16) | (b1 & 0xFFFF0000u);
   }
 };

@@ -11,11 +11,12 @@ const KernelOps *ops_f16sr() { return Launch<half_sr>::table(); }
 __global__ void round_probe_kernel(int bf16, const float *__restrict__ x, const uint32_t *__restrict__ salt,
                                    uint16_t *__restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // salt[i] plays the node seed, direction 0
     if (bf16) {
-      const bf16_sr r = Store<bf16_sr>::st_at(x[i], salt[i]);
+      const bf16_sr r = Store<bf16_sr>::st_at(x[i], salt[i], 0);
       out[i] = __bfloat16_as_ushort(r.v);
     } else {
-      const half_sr r = Store<half_sr>::st_at(x[i], salt[i]);
+      const half_sr r = Store<half_sr>::st_at(x[i], salt[i], 0);
       out[i] = __half_as_ushort(r.v);
     }
   }

@@ -122,12 +122,13 @@ template <class S>
 __device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &p, int x, int y,
                                            const typename Store<S>::C (&h)[9]) {
   S *o = B + (size_t)y * p.pitch + x;
+  if constexpr (Dithers<S>::value) {
+    const uint32_t seed = dither_seed(fold9(h), x, y);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    if constexpr (Dithers<S>::value)
-      o[(size_t)k * p.plane] = Store<S>::st_at(h[k], node_salt(x, y, k));
-    else
-      o[(size_t)k * p.plane] = Store<S>::st(h[k]);
+    for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st_at(h[k], seed, k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[(size_t)k * p.plane] = Store<S>::st(h[k]);
   }
 }
 
@@ -206,12 +207,19 @@ __device__ __forceinline__ void update_pair(S *__restrict__ B, const StepParams 
   }
   bad |= !speed_ok(collide_model<MRT, LF2>(h, cf));
   S *o = B + (size_t)y * p.pitch + x;
+  if constexpr (Dithers<S>::value) {
+    uint32_t f0 = 0, f1 = 0;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    if constexpr (Dithers<S>::value)
-      Store<S>::st2_at(o + (size_t)k * p.plane, h[k].v, node_salt(x, y, k), node_salt(x + 1, y, k));
-    else
-      Store<S>::st2(o + (size_t)k * p.plane, h[k].v);
+    for (int k = 0; k < 9; ++k) {
+      f0 ^= __float_as_uint(h[k].v.x);
+      f1 ^= __float_as_uint(h[k].v.y);
+    }
+    const uint32_t s0 = dither_seed(f0, x, y), s1 = dither_seed(f1, x + 1, y);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Store<S>::st2_at(o + (size_t)k * p.plane, h[k].v, s0, s1, k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Store<S>::st2(o + (size_t)k * p.plane, h[k].v);
   }
 }
 
@@ -716,11 +724,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
           for (int k = 0; k < 9; ++k) h[k] = (C)0;
         }
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          if constexpr (Dithers<S>::value)
-            out[k * W + (x - x0)] = Store<S>::st_at(h[k], node_salt(x, y, k));
-          else
-            out[k * W + (x - x0)] = Store<S>::st(h[k]);
+        if constexpr (Dithers<S>::value) {
+          const uint32_t seed = dither_seed(fold9(h), x, y);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) out[k * W + (x - x0)] = Store<S>::st_at(h[k], seed, k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) out[k * W + (x - x0)] = Store<S>::st(h[k]);
         }
       }
       __syncwarp();

@@ -172,11 +172,14 @@ template <int BN, int CK, int STAGES>
 struct TcLayout {
   static constexpr uint32_t ACC_COLS = TmemCols<BN>::value;  // one accumulator
   static constexpr uint32_t NCOLS = 2 * ACC_COLS;            // two, double-buffered
-  static constexpr int A_BYTES = kTileM * CK * 2;
-  static constexpr int B_BYTES = BN * CK * 2;
+  // taps per stage: with 32-channel chunks a stage carries the three taps of
+  // one kernel row, so each pipeline handshake feeds six MMAs instead of two
+  static constexpr int TPS = CK == 32 ? 3 : 1;
+  static constexpr int A_BYTES = kTileM * CK * 2;  // one tap's input tile
+  static constexpr int B_BYTES = BN * CK * 2;      // one tap's weight tile
   static constexpr int A_OFF = 0;
-  static constexpr int B_OFF = STAGES * A_BYTES;
-  static constexpr int BAR_OFF = B_OFF + STAGES * B_BYTES;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
+  static constexpr int B_OFF = STAGES * TPS * A_BYTES;
+  static constexpr int BAR_OFF = B_OFF + STAGES * TPS * B_BYTES;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
   static constexpr int NBARS = 2 * STAGES + 5;
   static constexpr int BIAS_OFF = BAR_OFF + NBARS * 8 + 16;  // the bias of every output channel
   static constexpr int BYTES = BIAS_OFF + 512 * 4;
@@ -210,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   float *sbias = reinterpret_cast<float *>(smem + Lay::BIAS_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kchunks = cin / CK, kblocks = 9 * kchunks;
+  constexpr int TPS = Lay::TPS;
+  const int kchunks = cin / CK, kblocks = (9 / TPS) * kchunks;
   const int wtiles = (W + kTileM - 1) / kTileM;
   for (int o = threadIdx.x; o < nchunks * BN; o += blockDim.x) sbias[o] = bias ? bias[o] : 0.f;
   const uint32_t full0 = saddr(&bars[0]), empty0 = saddr(&bars[STAGES]);
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int wt = r1 % wtiles, r2 = r1 / wtiles;
         const int h = r2 % H, n = r2 / H;
         const int w0 = wt * kTileM, o0 = chunk * BN;
-        int tap = 0, c0 = 0;
+        int tap = 0, c0 = 0;  // first tap of the stage's group, channel chunk
         for (int kb = 0; kb < kblocks; ++kb, ++g) {
           const int s = g % STAGES;
           if (g >= STAGES && !mbar_wait(empty0 + 8 * s, ((g / STAGES) - 1) & 1, s_abort)) {
@@ -262,15 +266,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             stop = true;
             break;
           }
-          const int dy = tap / 3, dx = tap - 3 * dy;
-          mbar_expect_tx(full0 + 8 * s, (uint32_t)(Lay::A_BYTES + Lay::B_BYTES));
-          tma_load_4d(saddr(smem + Lay::A_OFF + s * Lay::A_BYTES), &tmap_x, full0 + 8 * s, c0, w0 + dx - 1,
-                      h + dy - 1, n);
-          tma_load_2d(saddr(smem + Lay::B_OFF + s * Lay::B_BYTES), &tmap_w, full0 + 8 * s, tap * cin + c0, o0);
+          mbar_expect_tx(full0 + 8 * s, (uint32_t)(TPS * (Lay::A_BYTES + Lay::B_BYTES)));
+#pragma unroll
+          for (int j = 0; j < TPS; ++j) {
+            const int tj = tap + j, dy = tj / 3, dx = tj - 3 * dy;
+            tma_load_4d(saddr(smem + Lay::A_OFF + (s * TPS + j) * Lay::A_BYTES), &tmap_x, full0 + 8 * s, c0,
+                        w0 + dx - 1, h + dy - 1, n);
+            tma_load_2d(saddr(smem + Lay::B_OFF + (s * TPS + j) * Lay::B_BYTES), &tmap_w, full0 + 8 * s,
+                        tj * cin + c0, o0);
+          }
           c0 += CK;
           if (c0 == cin) {
             c0 = 0;
-            ++tap;
+            tap += TPS;
           }
         }
       }
@@ -306,12 +314,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a = saddr(smem + Lay::A_OFF + s * Lay::A_BYTES);
-          const uint32_t bb = saddr(smem + Lay::B_OFF + s * Lay::B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < CK / 16; ++kk)  // K = 16 per MMA: 32 bytes further along the swizzled row
-            umma_bf16(acc, kmajor_desc(a + 32 * kk, Lay::SBO, Lay::SWZ),
-                      kmajor_desc(bb + 32 * kk, Lay::SBO, Lay::SWZ), idesc, (kb | kk) != 0);
+          for (int j = 0; j < TPS; ++j) {
+            const uint64_t ad = kmajor_desc(saddr(smem + Lay::A_OFF + (s * TPS + j) * Lay::A_BYTES), Lay::SBO, Lay::SWZ);
+            const uint64_t bd = kmajor_desc(saddr(smem + Lay::B_OFF + (s * TPS + j) * Lay::B_BYTES), Lay::SBO, Lay::SWZ);
+#pragma unroll
+            for (int kk = 0; kk < CK / 16; ++kk)  // K = 16 per MMA: 32 bytes (2 in the address field) further
+              umma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (kb | j | kk) != 0);
+          }
           umma_commit(empty0 + 8 * s);  // the stage is free once these MMAs have read it
           ++issued;
         }
@@ -554,12 +564,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t a = saddr(smem + Lay::A_OFF + s * Lay::A_BYTES);
-        const uint32_t b = saddr(smem + Lay::B_OFF + s * Lay::B_BYTES);
+        const uint64_t ad = mnmajor_desc(saddr(smem + Lay::A_OFF + s * Lay::A_BYTES), kWgBlockBytes);
+        const uint64_t bd = mnmajor_desc(saddr(smem + Lay::B_OFF + s * Lay::B_BYTES), kWgBlockBytes);
 #pragma unroll
-        for (int kk = 0; kk < kWgPix / 16; ++kk)  // 16 pixels = two 8-row groups = 1024 B further
-          umma_bf16(tmem, mnmajor_desc(a + 1024 * kk, kWgBlockBytes), mnmajor_desc(b + 1024 * kk, kWgBlockBytes),
-                    idesc, (kb | kk) != 0);
+        for (int kk = 0; kk < kWgPix / 16; ++kk)  // 16 pixels = two 8-row groups = 1024 B (64 in the field)
+          umma_bf16(tmem, ad + 64 * kk, bd + 64 * kk, idesc, (kb | kk) != 0);
         umma_commit(empty0 + 8 * s);
         ++issued;
       }
@@ -727,12 +736,12 @@ int conv_fwd(const void *x, int xs, const void *w, const float *bias, void *y, i
   if (bn == BN_ && ck == CK_)                                                                                \
     e = launch<BN_, CK_, ST_>(tx, tw, bias, yb, ys, mb, ms, N, H, W, cin, nchunks, relu, st);                \
   else
-  GBNN_TC_CASE(32, 32, 6)
-  GBNN_TC_CASE(64, 32, 6)
-  GBNN_TC_CASE(96, 32, 6)
-  GBNN_TC_CASE(128, 32, 6)
-  GBNN_TC_CASE(192, 32, 5)
-  GBNN_TC_CASE(256, 32, 4)
+  GBNN_TC_CASE(32, 32, 3)
+  GBNN_TC_CASE(64, 32, 2)
+  GBNN_TC_CASE(96, 32, 3)
+  GBNN_TC_CASE(128, 32, 3)
+  GBNN_TC_CASE(192, 32, 3)
+  GBNN_TC_CASE(256, 32, 2)
   GBNN_TC_CASE(32, 64, 4)
   GBNN_TC_CASE(64, 64, 4)
   GBNN_TC_CASE(96, 64, 4)
