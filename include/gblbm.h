@@ -119,8 +119,10 @@ typedef struct lbm_opts {
  * the force of step n is known only after step n+1: with INTERPOLATED the
  * history is empty after lbm_init_fields and holds F(0..k-1) after k steps
  * (HALFWAY: F(0..k)).  Single lattices only (not batches, not
- * lbm_step_noalloc), always on the direct step kernel (LBM_KERNEL_DIRECT
- * whatever opts.kernel asks), so that the TMA kernels carry no code for it. */
+ * lbm_step_noalloc).  With float storage it runs on the TMA kernel in the
+ * float default shapes (12, 2, 4), (10, 2, 4) and (8, 2, 4); in every other
+ * case on the direct step kernel (LBM_KERNEL_DIRECT whatever opts.kernel
+ * asks), so that the 16-bit TMA kernels carry no code for it. */
 #define LBM_BOUNCE_HALFWAY 0
 #define LBM_BOUNCE_INTERPOLATED 1
 

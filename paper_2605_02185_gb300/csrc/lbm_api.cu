@@ -66,7 +66,11 @@ int find_shape(int kernel, int ncw, int cpt, int stages) {
 // slots) and capture the multi-step graph.
 int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
   if (kernel == LBM_KERNEL_AUTO) kernel = LBM_KERNEL_TMA;
-  if (c->qmap) kernel = LBM_KERNEL_DIRECT;  // interpolated bounce-back: direct kernel only
+  // interpolated bounce-back: the TMA kernel where it is built for this
+  // storage type and shape, else the direct kernel
+  if (c->qmap && (kernel != LBM_KERNEL_TMA ||
+                  c->ops->tma_interp(shape, 0, nullptr, nullptr, c->p, nullptr, 1) != cudaSuccess))
+    kernel = LBM_KERNEL_DIRECT;
   int seg;
   if (kernel == LBM_KERNEL_DIRECT) {
     seg = kDirectThreads;
@@ -120,6 +124,7 @@ cudaError_t launch_step(lbm_ctx *c, int from) {
   void *B = c->buf[from ^ 1];
   if (c->kernel == LBM_KERNEL_DIRECT) return c->ops->direct(A, B, c->p, c->stream);
   if (c->kernel == LBM_KERNEL_TMA_BULK) return c->ops->tma_bulk(c->shape, c->grid, A, B, c->p, c->stream);
+  if (c->qmap) return c->ops->tma_interp(c->shape, c->grid, A, B, c->p, c->stream, 0);
   return c->ops->tma(c->shape, c->grid, A, B, c->p, c->stream);
 }
 

@@ -116,19 +116,14 @@ template <> struct Store<double> {
 struct half_sr { __half v; };
 struct bf16_sr { __nv_bfloat16 v; };
 
-// The integer finaliser "lowbias32" (C. Wellons, hash-prospector, 2018).
-__device__ __forceinline__ uint32_t mix32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
-}
 // Per-node seed: the bits of the node's nine post-collision offsets folded
-// together with its position, then mixed.
+// together with its position, then one xorshift-multiply round (the first
+// round of the integer finaliser "lowbias32", C. Wellons, hash-prospector,
+// 2018); the per-direction multiply in dither() completes the mix.
 __device__ __forceinline__ uint32_t dither_seed(uint32_t fold, int x, int y) {
-  return mix32(fold ^ ((uint32_t)x * 0x9E3779B1u + (uint32_t)y * 0x85EBCA77u));
+  uint32_t z = fold ^ ((uint32_t)x * 0x9E3779B1u + (uint32_t)y * 0x85EBCA77u);
+  z ^= z >> 16;
+  return z * 0x7feb352du;
 }
 __device__ __forceinline__ uint32_t fold9(const float (&h)[9]) {
   uint32_t f = 0;
@@ -147,6 +142,13 @@ template <int DROP>
 __device__ __forceinline__ uint32_t dither(uint32_t bits, uint32_t seed, int k) {
   return bits + ((seed * dir_mul(k)) >> (32 - DROP));
 }
+// The same for binary16 storage of 2^12 h: the scaling by 2^12 is an add to
+// the fp32 exponent field (exact for every normal float; zero and float
+// subnormals become values far below the binary16 range, which truncate to
+// zero as before).
+__device__ __forceinline__ uint32_t dither_half(float v, uint32_t seed, int k) {
+  return __float_as_uint(v) + (12u << 23) + ((seed * dir_mul(k)) >> 19);
+}
 __device__ __forceinline__ uint32_t cvt_rz_half2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
@@ -158,16 +160,14 @@ template <> struct Store<half_sr> {
   __device__ static __forceinline__ C ld(half_sr v) { return __fmul_rn(__half2float(v.v), kHalfInv); }
   __device__ static __forceinline__ half_sr st(C v) { return {__float2half_rn(__fmul_rn(v, kHalfScale))}; }
   __device__ static __forceinline__ half_sr st_at(C v, uint32_t seed, int k) {
-    const uint32_t b = dither<13>(__float_as_uint(__fmul_rn(v, kHalfScale)), seed, k);
-    return {__float2half_rz(__uint_as_float(b))};
+    return {__float2half_rz(__uint_as_float(dither_half(v, seed, k)))};
   }
   __device__ static __forceinline__ float2 ld2(const half_sr *p) {
     return __fmul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(p)), make_float2(kHalfInv, kHalfInv));
   }
   __device__ static __forceinline__ void st2_at(half_sr *p, float2 v, uint32_t seed0, uint32_t seed1, int k) {
-    const float2 s = __fmul2_rn(v, make_float2(kHalfScale, kHalfScale));
-    const uint32_t b0 = dither<13>(__float_as_uint(s.x), seed0, k), b1 = dither<13>(__float_as_uint(s.y), seed1, k);
-    *reinterpret_cast<uint32_t *>(p) = cvt_rz_half2(__uint_as_float(b0), __uint_as_float(b1));
+    *reinterpret_cast<uint32_t *>(p) =
+        cvt_rz_half2(__uint_as_float(dither_half(v.x, seed0, k)), __uint_as_float(dither_half(v.y, seed1, k)));
   }
 };
 template <> struct Store<bf16_sr> {

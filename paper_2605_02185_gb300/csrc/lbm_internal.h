@@ -41,6 +41,11 @@ struct KernelOps {
   // nodes per thread and chunk of the single-lattice TMA kernel: its row
   // tile is tma_pair * warps * 32 * cells-per-thread nodes wide
   int tma_pair;
+  // the TMA kernel with interpolated bounce-back (prep != 0: only set its
+  // shared-memory limit); cudaErrorNotSupported for storage types and
+  // shapes it is not built for
+  cudaError_t (*tma_interp)(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st,
+                            int prep);
 };
 
 // Look up (once per device) the address of lbm_step_noalloc's static

@@ -3,6 +3,8 @@
 // instantiates them for one type and exports a KernelOps table.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -269,7 +271,10 @@ template <class S> struct TmaPair { static constexpr int nodes = sizeof(S) == 2 
 // (any x shift, no bank conflicts: consecutive lanes read consecutive
 // elements), apply the boundary rules, collide and store straight to HBM
 // with coalesced stores, then release the stage.  Every wait is bounded.
-template <class S, int NCW, int CPT, int STAGES, int MRT>
+// INTERP: general nodes take the interpolated bounce-back of pull(); the one
+// extra population it needs from a neighbour, f*_opp(k)(x + c_k), lies in the
+// staged row of plane opp(k), the others are the node's own (read from A).
+template <class S, int NCW, int CPT, int STAGES, int MRT, bool INTERP = false>
 __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__ A, S *__restrict__ B, StepParams p) {
   using C = typename Store<S>::C;
   constexpr int PX = TmaPair<S>::nodes;  // adjacent nodes per thread and chunk
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
           if (plain_span(p, xw, xw + 31, y))
             update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
           else if (x < p.nx)
-            update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+            update_node<MRT, S, decltype(fetch), INTERP>(A, B, p, x, y, cf, fetch, fx, fy, bad);
         }
       }
       __syncwarp();
@@ -980,6 +985,39 @@ struct Launch {
     return n < m ? n : m;
   }
 
+  // Interpolated bounce-back on the TMA kernel: float storage, the shapes
+  // the library picks by default for float ((12,2,4), (10,2,4), (8,2,4)).
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t tma_interp_one(int grid, const void *A, void *B, const StepParams &p, cudaStream_t st, bool prep) {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    if (prep) {
+      const cudaError_t e = cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES, 0, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(step_tma<S, NCW, CPT, STAGES, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
+    }
+    if (p.mrt)
+      step_tma<S, NCW, CPT, STAGES, 1, true><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    else
+      step_tma<S, NCW, CPT, STAGES, 0, true><<<grid, (NCW + 1) * 32, smem, st>>>((const S *)A, (S *)B, p);
+    return cudaGetLastError();
+  }
+  // prep != 0: only set the shared-memory limit (and so report whether this
+  // storage type and shape have the kernel: cudaErrorNotSupported if not)
+  static cudaError_t tma_interp(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st,
+                                int prep) {
+    if constexpr (std::is_same<S, float>::value) {
+      switch (shape) {
+        case 6: return tma_interp_one<8, 2, 4>(grid, A, B, p, st, prep != 0);
+        case 12: return tma_interp_one<12, 2, 4>(grid, A, B, p, st, prep != 0);
+        case 15: return tma_interp_one<10, 2, 4>(grid, A, B, p, st, prep != 0);
+      }
+    }
+    return cudaErrorNotSupported;
+  }
+
   static cudaError_t tma(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
     switch (shape) {
 #define X(id, a, b, c) \
@@ -1185,7 +1223,7 @@ struct Launch {
                                   &smem,          &init,       &force,        &fields,   &mass_rows,
                                   &batch_direct,  &batch_tma,  &batch_prep, &init_device,
                                   &tma_bulk,      &bulk_prep,  &bulk_occupancy, &bulk_smem,
-                                  TmaPair<S>::nodes};
+                                  TmaPair<S>::nodes, &tma_interp};
     return &ops;
   }
 };

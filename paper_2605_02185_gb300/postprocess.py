@@ -15,10 +15,31 @@ import math
 import numpy as np
 
 
-def upward_crossings(cl) -> np.ndarray:
-    """Fractional indices where cl crosses zero from below (linear interpolation)."""
+# Hysteresis of the zero-crossing detector, as a fraction of max |Cl|: a
+# crossing counts only after the lift has been below -HYST max |Cl| since the
+# previous one, so noise on the history (16-bit storage with stochastic
+# rounding) does not split one crossing into several.
+HYST = 0.05
+
+
+def upward_crossings(cl, hysteresis: float | None = None) -> np.ndarray:
+    """Fractional indices where cl crosses zero from below (linear
+    interpolation), each after cl went below -hysteresis (default HYST max |cl|)."""
     c = np.asarray(cl, np.float64)
+    if len(c) < 2:
+        return np.zeros(0)
+    eps = HYST * float(np.max(np.abs(c))) if hysteresis is None else hysteresis
     i = np.nonzero((c[:-1] < 0.0) & (c[1:] >= 0.0))[0]
+    if eps > 0.0 and len(i):
+        below = np.nonzero(c <= -eps)[0]
+        # keep crossing i if some sample in (previous kept crossing, i] is <= -eps
+        keep, last = [], -1
+        for j in i:
+            k = np.searchsorted(below, last + 1)
+            if k < len(below) and below[k] <= j:
+                keep.append(j)
+                last = j
+        i = np.asarray(keep, dtype=np.int64)
     return i + (-c[i]) / (c[i + 1] - c[i])
 
 
@@ -115,8 +136,18 @@ def statistics(cd, cl, D: float, U: float, periods: int | None = None) -> dict:
     w_cd, w_cl = cd[a:b + 1], cl[a:b + 1]
     T_zc = period_from_crossings(cl[a:b + 1]) if b > a else math.nan
     T_fft = period_from_spectrum(cl[a:b + 1]) if b > a else math.nan
+    # amplitude of the lift's fundamental over the window (least-squares fit
+    # of one harmonic at the spectral period): unlike (max - min) / 2 it does
+    # not grow with noise on the history
+    h1 = math.nan
+    if len(w_cl) > 8 and T_fft == T_fft:
+        t = np.arange(len(w_cl), dtype=np.float64)
+        basis = np.stack([np.cos(2 * math.pi * t / T_fft), np.sin(2 * math.pi * t / T_fft), np.ones_like(t)], 1)
+        coef, *_ = np.linalg.lstsq(basis, w_cl, rcond=None)
+        h1 = float(math.hypot(coef[0], coef[1]))
     return {"cd_mean": float(w_cd.mean()) if len(w_cd) else math.nan,
             "cl_amp": float(0.5 * (w_cl.max() - w_cl.min())) if len(w_cl) else math.nan,
+            "cl_amp_h1": h1,
             "st": D / (U * T_fft) if T_fft == T_fft else math.nan,
             "st_zc": D / (U * T_zc) if T_zc == T_zc else math.nan,
             "window": (a, b)}

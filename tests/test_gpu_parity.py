@@ -410,13 +410,40 @@ def test_interpolated_small_cylinder_mrt():
     compare_interpolated(wl, 1000, pops, F, fields, tol_f=1e-5 * wl.U, tol_F=1e-4, mrt=True)
 
 
-def test_interpolated_bounce_back_runs_on_the_direct_kernel():
+def test_interpolated_bounce_back_kernel_choice():
+    """Float storage: the TMA kernel in its default shapes; 16-bit storage
+    and other shapes: the direct kernel."""
     wl = W.random_case(97, 33, seed=3, bc=W.BC_FREESLIP, D=8)
-    lat = lbm.lattice_for(wl, kernel=lbm.LBM_KERNEL_TMA, **INTERP)
-    try:
-        assert lat.kernel_info()["kernel"] == lbm.LBM_KERNEL_DIRECT
-    finally:
-        lat.close()
+    for kw, want in ((dict(kernel=lbm.LBM_KERNEL_TMA), lbm.LBM_KERNEL_TMA),
+                     (dict(kernel=lbm.LBM_KERNEL_TMA, storage=lbm.LBM_F16_OFS), lbm.LBM_KERNEL_DIRECT),
+                     (dict(kernel=lbm.LBM_KERNEL_TMA, shape=(16, 2, 2)), lbm.LBM_KERNEL_DIRECT)):
+        lat = lbm.lattice_for(wl, **INTERP, **kw)
+        try:
+            assert lat.kernel_info()["kernel"] == want, kw
+        finally:
+            lat.close()
+
+
+@pytest.mark.parametrize("mrt", [False, True], ids=["bgk", "mrt"])
+def test_interpolated_tma_kernel_matches_direct(mrt):
+    """Interpolated bounce-back on the TMA kernel: the same per-node
+    arithmetic as the direct kernel, identical bits, in each shape it is
+    built for, with the link-owning rows spread over several row tiles."""
+    wl = W.random_case(1025, 61, seed=12, bc=W.BC_ZOUHE, D=24)
+    coll = MRT if mrt else {}
+    kw = dict(**INTERP, **coll)
+    ref, Fr, _ = gpu_run_interpolated(wl, 30, kernel=lbm.LBM_KERNEL_DIRECT, **coll)
+    for shape in [(12, 2, 4), (10, 2, 4), (8, 2, 4)]:
+        lat = lbm.lattice_for(wl, kernel=lbm.LBM_KERNEL_TMA, shape=shape, **kw)
+        try:
+            assert lat.kernel_info()["kernel"] == lbm.LBM_KERNEL_TMA
+            lat.init_fields(*wl.initial_fields())
+            lat.step(30)
+            lat.sync()
+            assert np.array_equal(lat.get_populations(), ref), shape
+            assert np.array_equal(lat.forces_raw(0, 30), Fr), shape
+        finally:
+            lat.close()
 
 
 def test_every_tma_shape_matches_direct():

@@ -52,3 +52,14 @@ def test_periodicity_ignores_periods_outside_the_shedding_range():
     assert PP.periodic_index(ring, period_range=rng) is None
     shed = 0.3 * np.sin(2 * math.pi * np.arange(20000) / 1900.0)
     assert PP.periodic_index(shed, period_range=rng) is not None
+
+
+def test_first_harmonic_amplitude_ignores_noise():
+    n = np.arange(40000)
+    rng = np.random.default_rng(1)
+    cl = 0.3 * np.sin(2 * math.pi * n / 2000.0 + 0.4) + 0.005 * rng.standard_normal(n.size)
+    cd = 1.4 + 0.01 * np.cos(4 * math.pi * n / 2000.0)
+    st = PP.statistics(cd, cl, 20, 0.05, periods=10)
+    assert abs(st["cl_amp_h1"] - 0.3) < 0.003       # the fundamental
+    assert st["cl_amp"] > 0.31                       # (max - min) / 2 picks up the noise peaks
+    assert abs(st["st"] - 20 / (0.05 * 2000)) < 1e-3
