@@ -545,7 +545,7 @@ def run_warmstart(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    cfg = WS.Config(snapshots=args.snapshots, train_cases=args.cases if args.cases != 64 else 32)
+    cfg = WS.Config(snapshots=args.snapshots, train_cases=args.cases if args.cases != 64 else 32, iters=args.iters)
     logs = []
     net, info = WS.train(cfg, device, log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
     rows, summary = WS.evaluate(net, cfg, n_eval=args.eval_cases, device=device,
@@ -742,6 +742,7 @@ def main(argv=None):
                     help="statistics workload: body bounce-back (interpolated runs on the direct kernel)")
     ap.add_argument("--snapshots", type=int, default=20000, help="warmstart workload: training snapshots")
     ap.add_argument("--eval-cases", type=int, default=16, help="warmstart workload: held-out Re values")
+    ap.add_argument("--iters", type=int, default=0, help="warmstart workload: training iterations (0: snapshots/4)")
     ap.add_argument("--cases", type=int, default=64, help="batch workload: number of cases")
     ap.add_argument("--tune", action="store_true", help="batch workload: autotune the kernel shape first")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
