@@ -728,7 +728,8 @@ def main(argv=None):
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="0: the library's tuned default")
     ap.add_argument("--workload", default="throughput",
-                    choices=["throughput", "production", "parity", "batch", "warmstart", "statistics", "network"])
+                    choices=["throughput", "throughput_half", "production", "parity", "batch", "warmstart",
+                             "statistics", "network"])
     ap.add_argument("--net-batch", type=int, default=4, help="network workload: samples per batch")
     ap.add_argument("--runs", default="freeslip:f64,freeslip:f32,freeslip:f16,freeslip:bf16,periodic:f32,"
                                       "zouhe:f32,movingwall:f32",
@@ -762,7 +763,8 @@ def main(argv=None):
         return run_statistics(args)
     if args.workload == "network":
         return run_network(args)
-    wl = {"throughput": W.THROUGHPUT_D400, "production": W.PRODUCTION_D80, "parity": W.PARITY_D10}[args.workload]
+    wl = {"throughput": W.THROUGHPUT_D400, "throughput_half": W.THROUGHPUT_D200, "production": W.PRODUCTION_D80,
+          "parity": W.PARITY_D10}[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_ours(args, wl)

@@ -415,15 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // 128 rows of one M tile are four blocks of 32 rows, each block one
 // (tap, 32-channel chunk) pair -- so the nine taps of a 32-channel layer
 // fill M with little waste -- and N is the whole output-channel count
-// (<= 256).  Per K step of 64 pixels (a segment of one image row) the TMA
-// engine copies the four shifted 64 x 32 input boxes and the 64 x N output
+// (<= 256).  Per K step of 128 pixels (a segment of one image row) the TMA
+// engine copies the four shifted 128 x 32 input boxes and the 128 x N output
 // gradient; in NHWC both arrive channel-contiguous, i.e. M- and N-major
-// (MN-major, 64-byte swizzle: 32-channel atoms 64 x 64 B apart, 8-pixel row
+// (MN-major, 64-byte swizzle: 32-channel atoms 128 x 64 B apart, 8-pixel row
 // groups 512 B apart).  Each CTA sums a contiguous range of K steps (split
 // K); the epilogue warp of TMEM quarter q owns row block q and adds its
 // 32 x N partial sums to gw with coalesced float atomics (order not fixed).
-constexpr int kWgPix = 64;                   // pixels per K step
-constexpr int kWgBlockBytes = kWgPix * 32 * 2;  // one 64-pixel x 32-channel box
+constexpr int kWgPix = 128;                  // pixels per K step
+constexpr int kWgBlockBytes = kWgPix * 32 * 2;  // one 128-pixel x 32-channel box
 
 template <int BN, int STAGES>
 struct WgLayout {
@@ -811,10 +811,10 @@ int conv_wgrad(const void *x, int xs, const void *gy, int gs, float *gw, float *
   if (splits > 65535) splits = 65535;
   cudaError_t e;
   switch (bn) {
-    case 32: e = launch_wgrad<32, 8>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
-    case 64: e = launch_wgrad<64, 8>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
-    case 128: e = launch_wgrad<128, 6>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
-    default: e = launch_wgrad<256, 4>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
+    case 32: e = launch_wgrad<32, 5>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
+    case 64: e = launch_wgrad<64, 4>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
+    case 128: e = launch_wgrad<128, 3>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
+    default: e = launch_wgrad<256, 2>(tx, tg, gw, H, W, cin, cout, nblocks, mtiles, ksteps, splits, st); break;
   }
   if (e != cudaSuccess) return -2;
   if (gb) {

@@ -133,6 +133,10 @@ PRODUCTION_D80 = cylinder_case(80, 0.05, 100.0, seed=2, perturb=1e-3, steps=300_
 # Throughput case: 128M cells, Re = 100, D = 400, U = 0.04 (Eq. 17 gives tau = 0.98).
 THROUGHPUT_D400 = cylinder_case(400, 0.04, 100.0, seed=3, perturb=1e-3, steps=50_000,
                                 name="cyl_Re100_D400_16000x8000")
+# The throughput geometry at half the size (32M cells, 2.3 GB of FP32
+# populations): small enough for counter captures, far above L2.
+THROUGHPUT_D200 = cylinder_case(200, 0.04, 100.0, seed=3, perturb=1e-3, steps=50_000,
+                                name="cyl_Re100_D200_8000x4000")
 # Warm-start grid: D = 40, U = 0.05, 1600 x 800.
 WARMSTART_D40 = cylinder_case(40, 0.05, 100.0, seed=5, perturb=1e-3,
                               name="cyl_D40_1600x800")
