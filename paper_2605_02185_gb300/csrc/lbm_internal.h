@@ -80,7 +80,9 @@ const KernelOps *ops_bf16sr();
   X(15, 10, 2, 4)           \
   X(16, 13, 1, 6)           \
   X(17, 13, 1, 4)           \
-  X(18, 10, 1, 6)
+  X(18, 10, 1, 6)           \
+  X(19, 13, 2, 3)           \
+  X(20, 13, 2, 2)
 
 // Shapes of the TMA-load + TMA-bulk-store kernel X(id, warps, cells/thread, stages).
 #define GBLBM_TMA_BULK_SHAPES(X) \
