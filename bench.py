@@ -391,7 +391,8 @@ def extras(args, workload, device, stream):
     steps = max(args.steps, 20)
     rho0, u0, v0 = workload.initial_fields()
     forms = {}
-    for name, st in (("f16", lbm.LBM_F16_OFS), ("bf16", lbm.LBM_BF16_OFS), ("f16sr", lbm.LBM_F16_SR)):
+    for name, st in (("f16", lbm.LBM_F16_OFS), ("bf16", lbm.LBM_BF16_OFS), ("f16sr", lbm.LBM_F16_SR),
+                     ("bf16sr", lbm.LBM_BF16_SR)):
         lat = lbm.lattice_for(workload, storage=st, stream=stream, device=device)
         lat.init_fields(rho0, u0, v0)
         lat.step(args.warmup)
