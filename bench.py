@@ -597,7 +597,13 @@ def run_network(args):
     dims = {"c1": 0, "d1": 0, "he": 0, "c2": 1, "d2": 1, "c3": 2, "d3": 2, "c4": 3}
     rows = []
     reps = max(3, args.steps // 4)
+    layers = set(args.layers.split(",")) if args.layers else None
+    impls = [("tcgen05", nn.IMPL_AUTO), ("mma_sync", nn.IMPL_MMA_SYNC)]
+    if args.conv_impl != "both":
+        impls = [i for i in impls if i[0] == args.conv_impl]
     for name, c in net.layers.items():
+        if layers is not None and name not in layers:
+            continue
         h, w = net.dims[dims[name[:2]]]
         flops = 2.0 * N * h * w * 9 * c.cin * c.cout
         x = torch.from_numpy(rng.standard_normal((N, h, w, c.cin)).astype(np.float32)).to(device, torch.bfloat16)
@@ -610,7 +616,7 @@ def run_network(args):
             "dgrad": lambda: nn.conv3x3_dgrad(gy, c.cout, c.wf16, gx, c.cin, N, h, w, c.cin, c.cout),
             "wgrad": lambda: nn.conv3x3_wgrad(x, c.cin, gy, c.cout, c.gw, c.gb, N, h, w, c.cin, c.cout),
         }
-        for impl_name, impl in (("tcgen05", nn.IMPL_AUTO), ("mma_sync", nn.IMPL_MMA_SYNC)):
+        for impl_name, impl in impls:
             nn.set_conv_impl(impl)
             for kind, fn in calls.items():
                 for _ in range(2):
@@ -632,21 +638,22 @@ def run_network(args):
             net.adam_step(1e-4)
 
     iters = {}
-    for impl_name, impl in (("tcgen05", nn.IMPL_AUTO), ("mma_sync", nn.IMPL_MMA_SYNC)):
+    for impl_name, impl in ([] if layers is not None else impls):
         nn.set_conv_impl(impl)
         iteration(2)
         iters[impl_name] = time_steps(iteration, reps, stream) / reps
     nn.set_conv_impl(nn.IMPL_AUTO)
     assert nn.status(reset=True) == 0
     fl = 3 * net.flops_per_sample() * N
+    it = iters.get("tcgen05")
     print(json.dumps({
         "metric": "warm-start network training iteration (3x3 conv fwd + both gradients), BF16 tensor cores",
-        "value": fl / iters["tcgen05"] / 1e12, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1,
+        "value": fl / it / 1e12 if it else None, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1,
         "data": "synthetic", "dtype": "bf16 (FP32 accumulation)",
         "config": {"workload": f"warm-start U-Net, N = {N}, {H} x {W}", "reps": reps},
         "iteration_ms": {k: v * 1e3 for k, v in iters.items()},
         "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "peak_source": src,
-                     "frac": fl / iters["tcgen05"] / 1e12 / peak},
+                     "frac": fl / it / 1e12 / peak if it else None},
         "layers": rows}), flush=True)
     return 0
 
@@ -740,6 +747,10 @@ def main(argv=None):
                     choices=["throughput", "throughput_half", "production", "parity", "batch", "warmstart",
                              "statistics", "network"])
     ap.add_argument("--net-batch", type=int, default=4, help="network workload: samples per batch")
+    ap.add_argument("--layers", default="", help="network workload: comma list of layers to time (default all, "
+                                                 "and the whole training iteration)")
+    ap.add_argument("--conv-impl", choices=["both", "tcgen05", "mma_sync"], default="both",
+                    help="network workload: kernel families to time")
     ap.add_argument("--runs", default="freeslip:f64,freeslip:f32,freeslip:f16,freeslip:bf16,periodic:f32,"
                                       "zouhe:f32,movingwall:f32",
                     help="statistics workload: comma list of top/bottom rule:storage")
