@@ -351,6 +351,7 @@ def run_ours(args, workload):
                    "tau": workload.tau, "Re": workload.Re, "bc": "freeslip", "storage": args.storage + " offsets",
                    "collision": args.collision,
                    "kernel": info, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "gpu": torch.cuda.get_device_name(device), "seed": workload.seed,
                    "l2": f"inputs {bytes_step / 2 / 1e9:.1f} GB of populations read per step, far above the "
                          "129 MB L2: no flush needed"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
