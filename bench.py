@@ -555,9 +555,23 @@ def run_warmstart(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    cfg = WS.Config(snapshots=args.snapshots, train_cases=args.cases if args.cases != 64 else 32, iters=args.iters)
+    cfg = WS.Config(snapshots=args.snapshots, train_cases=args.cases if args.cases != 64 else 32, iters=args.iters,
+                    init_mode=args.ws_init)
     logs = []
-    net, info = WS.train(cfg, device, log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
+    if args.ws_load:
+        # a network trained by an earlier run (its state() saved with --ws-save)
+        import numpy as np
+        from paper_2605_02185_gb300 import nn
+        net = nn.WarmStartNet(cfg.batch, 20 * cfg.D, 40 * cfg.D, device, seed=cfg.seed, zero_head=True)
+        with np.load(args.ws_load) as z:
+            net.load_state({k: z[k] for k in z.files})
+        info = {"loaded": args.ws_load, "losses": [(0, float("nan")), (0, float("nan"))], "spinup_s": 0.0,
+                "fill_s": 0.0, "train_s": 0.0, "snapshots": 0}
+    else:
+        net, info = WS.train(cfg, device, log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
+        if args.ws_save:
+            import numpy as np
+            np.savez(args.ws_save, **net.state())
     rows, summary = WS.evaluate(net, cfg, n_eval=args.eval_cases, device=device,
                                 log=lambda m: logs.append(m) or print(m, file=sys.stderr, flush=True))
     if rank == 0:
@@ -568,7 +582,7 @@ def run_warmstart(args):
             "data": "synthetic", "dtype": "bf16 network, f32 lattice",
             "config": {"workload": f"cylinder D = {cfg.D}, {40 * cfg.D} x {20 * cfg.D}, U = {cfg.U}, "
                                    f"Re in [{cfg.re_lo}, {cfg.re_hi}], MRT collision", "train_cases": cfg.train_cases,
-                       "snapshots": info["snapshots"], "batch": cfg.batch},
+                       "snapshots": info["snapshots"], "batch": cfg.batch, "init_mode": cfg.init_mode},
             "summary": summary, "train": {k: v for k, v in info.items() if k != "losses"},
             "training_cost_s": info["spinup_s"] + info["fill_s"] + info["train_s"],
             "loss_first_last": [info["losses"][0], info["losses"][-1]], "cases": rows}), flush=True)
@@ -765,6 +779,10 @@ def main(argv=None):
     ap.add_argument("--snapshots", type=int, default=20000, help="warmstart workload: training snapshots")
     ap.add_argument("--eval-cases", type=int, default=16, help="warmstart workload: held-out Re values")
     ap.add_argument("--iters", type=int, default=0, help="warmstart workload: training iterations (0: snapshots/4)")
+    ap.add_argument("--ws-save", default="", help="warmstart workload: save the trained weights (npz)")
+    ap.add_argument("--ws-load", default="", help="warmstart workload: evaluate weights saved by --ws-save")
+    ap.add_argument("--ws-init", choices=["noneq", "eq", "rho1"], default="noneq",
+                    help="warmstart workload: how the prediction starts the lattice")
     ap.add_argument("--cases", type=int, default=64, help="batch workload: number of cases")
     ap.add_argument("--tune", action="store_true", help="batch workload: autotune the kernel shape first")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

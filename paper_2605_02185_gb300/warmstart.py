@@ -62,6 +62,11 @@ class Config:
     vel_factor: float = 0.2   # velocity targets (u - U, v) / (vel_factor U)
     warmup: int = 300         # training iterations of linear learning-rate warm-up
     wave_len: float = 5.0     # wavelength (in D) of the travelling-wave input basis; 0: none
+    # how the prediction starts the lattice: "noneq" f_eq(rho, u) + f_neq(grad u);
+    # "eq" f_eq(rho, u) only; "rho1" f_eq(1, u) + f_neq(grad u), the predicted
+    # density dropped (so that no pressure error of the prediction is started
+    # as a sound wave)
+    init_mode: str = "noneq"
 
     @property
     def rho_scale(self) -> float:
@@ -344,7 +349,9 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
                          fr[2], stream)
     stream.synchronize()
     t_inf = time.perf_counter() - t0
-    lbm.lbm_init_fields_device(lat.h, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr(), True)
+    if cfg.init_mode == "rho1":
+        fr[0].fill_(1.0)
+    lbm.lbm_init_fields_device(lat.h, fr[0].data_ptr(), fr[1].data_ptr(), fr[2].data_ptr(), cfg.init_mode != "eq")
     n_warm, t_warm, st_warm = run_to_periodic(lat, wl, cfg.eval_max, cfg.chunk, t0, cfg.settle_periods,
                                               cfg.stat_periods)
     lat.sync()
