@@ -269,7 +269,8 @@ def run_ours(args, workload):
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
     nx, ny = workload.nx, workload.ny
     stream = torch.cuda.Stream(device)
-    kernel = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "direct": lbm.LBM_KERNEL_DIRECT}[args.kernel]
+    kernel = {"auto": lbm.LBM_KERNEL_AUTO, "tma": lbm.LBM_KERNEL_TMA, "direct": lbm.LBM_KERNEL_DIRECT,
+              "wave": lbm.LBM_KERNEL_TMA_WAVE}[args.kernel]
     coll = lbm.LBM_COLLIDE_MRT if args.collision == "mrt" else lbm.LBM_COLLIDE_BGK
     lat = lbm.lattice_for(workload, storage=storage, kernel=kernel, shape=shape, ctas_per_sm=args.ctas_per_sm,
                           stream=stream, device=device, collision=coll)
@@ -753,7 +754,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16", "f64", "f16sr", "bf16sr"], default="f32")
-    ap.add_argument("--kernel", choices=["auto", "tma", "direct"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "tma", "direct", "wave"], default="auto",
+                    help="wave: the multi-step TMA kernel (up to 64 steps per cooperative launch)")
     ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
                     help="bgk: Eq. 2 (the default hot path); mrt: the paper's Eq. 6 with its rates")
     ap.add_argument("--shape", default="", help="TMA shape: compute warps,cells per thread,stages")

@@ -78,6 +78,18 @@ extern "C" {
 #define LBM_KERNEL_TMA 2    /* persistent; bulk-async (TMA) row staging */
 #define LBM_KERNEL_TMA_BULK 3 /* TMA row staging and TMA bulk stores of the new rows
                                  (single lattices; not for batches) */
+#define LBM_KERNEL_TMA_WAVE 4 /* the TMA kernel run for up to 64 steps per launch
+                                 (single lattices; not for batches): a cooperative
+                                 launch in which each CTA owns a contiguous band of
+                                 row tiles and, between steps, waits (bounded) only
+                                 for the CTAs whose rows border its own, so steps
+                                 are not separated by a launch, its pipeline fill
+                                 and its tail.  Results are bit-identical to
+                                 LBM_KERNEL_TMA.  Built for the shapes that
+                                 lbm_kernel_shapes_for lists; half-way
+                                 bounce-back only (interpolated bounce-back runs
+                                 on the kernels named under lbm_opts.bounce).
+                                 No CUDA graph is captured for it. */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -236,7 +248,7 @@ int lbm_get_kernel(lbm_ctx *ctx, int *out6);
  * cells per thread, stages) into out; *count receives how many exist. */
 int lbm_kernel_shapes(int *out, int cap, int *count);
 
-/* The same for LBM_KERNEL_TMA or LBM_KERNEL_TMA_BULK. */
+/* The same for LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK or LBM_KERNEL_TMA_WAVE. */
 int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count);
 
 /* Failure-path testing (no counterpart in the paper).  Every wait of the
@@ -249,14 +261,15 @@ int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count);
  * of row tile `tile` (row * tiles per row + segment, as the kernel numbers
  * them) but never issues them, so the waits on that tile run out.  The
  * populations are then partly stale: restore a checkpoint or re-initialise.
- * The context must use LBM_KERNEL_TMA or LBM_KERNEL_TMA_BULK (LBM_ERR_ARG
- * otherwise).  tile < 0 and wait_seconds <= 0 restore normal operation. */
+ * The context must use LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK or
+ * LBM_KERNEL_TMA_WAVE (LBM_ERR_ARG otherwise).  tile < 0 and wait_seconds <= 0 restore normal operation. */
 int lbm_set_fault_injection(lbm_ctx *ctx, int64_t tile, double wait_seconds);
 
 /* The CUDA stream the context launches on (cudaStream_t). */
 int lbm_get_stream(lbm_ctx *ctx, void **stream);
 
-/* Step-kernel launches issued since creation (counts each kernel once). */
+/* Step-kernel launches issued since creation (counts each kernel once; a
+ * launch of LBM_KERNEL_TMA_WAVE counts 2, with its force reduction). */
 int lbm_launch_count(lbm_ctx *ctx, int64_t *count);
 
 /* Algorithmic bytes one step moves through HBM: 2 * 9 * element size per

@@ -22,7 +22,9 @@ using namespace gblbm;
 
 namespace {
 
-size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[8], int *slot_cap_out,
+constexpr int kLayoutParts = 10;
+
+size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[kLayoutParts], int *slot_cap_out,
               int *band_rows_out) {
   const int elem = elem_size(o->storage);
   const int pitch = (int)align_up((size_t)o->nx, 64);
@@ -35,6 +37,8 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   const long long cap = o->history_capacity > 0 ? o->history_capacity : (1ll << 20);
   const size_t hist = align_up((size_t)cap * 2 * sizeof(double), kAlign);
   const size_t ctrl = kAlign;
+  const size_t wave_slots = align_up((size_t)kWaveSteps * slot_cap * sizeof(double2), kAlign);
+  const size_t wave_prog = align_up((size_t)kWaveMaxGrid * sizeof(unsigned), kAlign);
   const int band_rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)o->ny, kBandCells / (size_t)o->nx));
   const size_t staging =
       align_up(std::max<size_t>((size_t)band_rows * o->nx * 3 * sizeof(double), (size_t)o->ny * sizeof(double)), kAlign);
@@ -46,7 +50,9 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   offs[4] = off; off += hist;
   offs[5] = off; off += ctrl;
   offs[6] = off; off += staging;
-  offs[7] = off;
+  offs[7] = off; off += wave_slots;
+  offs[8] = off; off += wave_prog;
+  offs[9] = off;
   *pitch_out = pitch;
   *slot_cap_out = slot_cap;
   *band_rows_out = band_rows;
@@ -82,6 +88,16 @@ int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
     if (occ <= 0) return LBM_ERR_ARG;
     ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
     seg = kTmaBulkShapes[shape].ncw * 32 * kTmaBulkShapes[shape].cpt;
+  } else if (kernel == LBM_KERNEL_TMA_WAVE) {
+    if (shape < 0 || shape >= kNumTmaShapes) return LBM_ERR_ARG;
+    if (c->ops->smem(shape) > 227 * 1024) return LBM_ERR_ARG;
+    const cudaError_t e = c->ops->wave_prep(shape);
+    if (e == cudaErrorNotSupported) return LBM_ERR_ARG;
+    CK(e);
+    const int occ = c->ops->wave_occupancy(shape);
+    if (occ <= 0) return LBM_ERR_ARG;
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, occ));
+    seg = c->ops->tma_pair * kTmaShapes[shape].ncw * 32 * kTmaShapes[shape].cpt;
   } else {
     if (shape < 0 || shape >= kNumTmaShapes) return LBM_ERR_ARG;
     if (c->ops->smem(shape) > 227 * 1024) return LBM_ERR_ARG;
@@ -109,13 +125,20 @@ int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
   if (p.nslots > c->slot_cap) return LBM_ERR_ARG;
   const long long nitems = (long long)c->ny * nseg;
   if (nitems > (1ll << 31) - 1) return LBM_ERR_ARG;
+  const int grid = kernel == LBM_KERNEL_DIRECT ? (int)nitems
+                                               : (int)std::min<long long>(nitems, (long long)c->sms * ctas_per_sm);
+  if (kernel == LBM_KERNEL_TMA_WAVE) {
+    if (grid > kWaveMaxGrid) return LBM_ERR_ARG;
+    // a new grid starts from cleared progress counters
+    CK(cudaMemsetAsync(c->wave_prog, 0, (size_t)kWaveMaxGrid * sizeof(unsigned), c->stream));
+    c->wave_base = 0;
+  }
   c->kernel = kernel;
   c->shape = shape;
   c->ctas_per_sm = ctas_per_sm;
   c->seg = seg;
   c->nseg = nseg;
-  c->grid = kernel == LBM_KERNEL_DIRECT ? (int)nitems
-                                         : (int)std::min<long long>(nitems, (long long)c->sms * ctas_per_sm);
+  c->grid = grid;
   return LBM_OK;
 }
 
@@ -128,13 +151,35 @@ cudaError_t launch_step(lbm_ctx *c, int from) {
   return c->ops->tma(c->shape, c->grid, A, B, c->p, c->stream);
 }
 
+// Steps [0, n) on the multi-step kernel, kWaveSteps per launch.
+int wave_steps(lbm_ctx *c, int64_t n) {
+  while (n > 0) {
+    const int k = (int)std::min<int64_t>(n, kWaveSteps);
+    if (c->wave_base > (1u << 30)) {  // keep counter differences far from 2^31
+      CK(cudaMemsetAsync(c->wave_prog, 0, (size_t)kWaveMaxGrid * sizeof(unsigned), c->stream));
+      c->wave_base = 0;
+    }
+    WaveParams w;
+    w.prog = c->wave_prog;
+    w.base = c->wave_base;
+    w.steps = k;
+    w.slots = c->wave_slots;
+    CK(c->ops->wave(c->shape, c->grid, c->buf[c->cur], c->buf[c->cur ^ 1], c->p, w, c->stream));
+    c->wave_base += (unsigned)k;
+    c->cur ^= k & 1;
+    c->launches += 2;
+    n -= k;
+  }
+  return LBM_OK;
+}
+
 int capture_graph(lbm_ctx *c) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
   int gs = c->o.graph_steps;
-  if (gs < 0) {
+  if (gs < 0 || c->kernel == LBM_KERNEL_TMA_WAVE) {  // the multi-step kernel needs no graph
     c->graph_steps = 0;
     return LBM_OK;
   }
@@ -186,7 +231,7 @@ int lbm_workspace_bytes(const lbm_opts *o, const uint8_t *mask, size_t *bytes) {
   rc = build_geometry(o, mask, &g);
   if (rc) return rc;
   int pitch, slot_cap, band_rows;
-  size_t offs[8];
+  size_t offs[kLayoutParts];
   *bytes = layout(o, g, &pitch, offs, &slot_cap, &band_rows);
   return LBM_OK;
 }
@@ -208,7 +253,7 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   c->ny = o->ny;
   c->elem = elem_size(o->storage);
   c->ops = ops_for(o->storage);
-  size_t offs[8];
+  size_t offs[kLayoutParts];
   c->ws_bytes = layout(o, c->geo, &c->pitch, offs, &c->slot_cap, &c->band_rows);
   c->plane = (long long)c->ny * c->pitch;
   c->hist_cap = o->history_capacity > 0 ? o->history_capacity : (1ll << 20);
@@ -242,6 +287,8 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   c->ctrl = (unsigned *)(base + offs[5]);
   c->staging = base + offs[6];
   c->staging_bytes = offs[7] - offs[6];
+  c->wave_slots = (double2 *)(base + offs[7]);
+  c->wave_prog = (unsigned *)(base + offs[8]);
   if (o->stream) {
     c->stream = (cudaStream_t)o->stream;
   } else {
@@ -369,6 +416,7 @@ int lbm_step(lbm_ctx *c, int64_t n) {
   if (!c || n < 0) return LBM_ERR_ARG;
   if (!c->inited) return LBM_ERR_STATE;
   CK(cudaSetDevice(c->dev));
+  if (c->kernel == LBM_KERNEL_TMA_WAVE) return wave_steps(c, n);
   while (n > 0) {
     if (c->graph && c->cur == 0 && n >= c->graph_steps) {
       CK(cudaGraphLaunch(c->graph, c->stream));
@@ -519,7 +567,7 @@ int lbm_set_populations(lbm_ctx *c, const void *src, size_t bytes, int64_t step)
 }
 
 int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int ctas_per_sm) {
-  if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA_WAVE) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
   int shape = kernel == LBM_KERNEL_TMA_BULK ? 0 : default_shape(c->o.storage, c->nx);
@@ -538,7 +586,8 @@ int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int cta
 
 int lbm_set_fault_injection(lbm_ctx *c, int64_t tile, double wait_seconds) {
   if (!c) return LBM_ERR_ARG;
-  if (c->kernel != LBM_KERNEL_TMA && c->kernel != LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (c->kernel != LBM_KERNEL_TMA && c->kernel != LBM_KERNEL_TMA_BULK && c->kernel != LBM_KERNEL_TMA_WAVE)
+    return LBM_ERR_ARG;
   if (tile >= (int64_t)c->ny * c->nseg || !(wait_seconds <= 60.0)) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
@@ -573,8 +622,17 @@ int lbm_kernel_shapes(int *out, int cap, int *count) {
 }
 
 int lbm_kernel_shapes_for(int kernel, int *out, int cap, int *count) {
-  if (kernel != LBM_KERNEL_TMA && kernel != LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (kernel != LBM_KERNEL_TMA && kernel != LBM_KERNEL_TMA_BULK && kernel != LBM_KERNEL_TMA_WAVE) return LBM_ERR_ARG;
   if (!count || cap < 0 || (cap > 0 && !out)) return LBM_ERR_ARG;
+  if (kernel == LBM_KERNEL_TMA_WAVE) {
+    *count = kNumWaveShapes;
+    for (int s = 0; s < kNumWaveShapes && s < cap; ++s) {
+      out[3 * s] = kWaveShapes[s].ncw;
+      out[3 * s + 1] = kWaveShapes[s].cpt;
+      out[3 * s + 2] = kWaveShapes[s].stages;
+    }
+    return LBM_OK;
+  }
   const TmaShape *list = kernel == LBM_KERNEL_TMA_BULK ? kTmaBulkShapes : kTmaShapes;
   const int n = kernel == LBM_KERNEL_TMA_BULK ? kNumTmaBulkShapes : kNumTmaShapes;
   *count = n;

@@ -196,6 +196,25 @@ template <> __device__ __forceinline__ bf16_sr ldg_s(const bf16_sr *p) {
   return {__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)))};
 }
 
+// L2-only load (ld.global.cg) of one stored value: for state written earlier
+// in the same launch (the multi-step kernel), where the non-coherent
+// read-only cache path must not be used.
+template <class S> __device__ __forceinline__ S ldcg_s(const S *p) {
+  if constexpr (sizeof(S) == 2) {
+    const unsigned short b = __ldcg(reinterpret_cast<const unsigned short *>(p));
+    S v;
+    __builtin_memcpy(&v, &b, 2);
+    return v;
+  } else {
+    return __ldcg(p);
+  }
+}
+// A node's own value of the previous step: a plain load, or (COH) ldcg_s.
+template <bool COH, class S> __device__ __forceinline__ S own_ld(const S *p) {
+  if constexpr (COH) return ldcg_s(p);
+  else return *p;
+}
+
 // Whether a storage type rounds stochastically (st_at / st2_at) or to
 // nearest (st / st2).
 template <class S> struct Dithers { static constexpr bool value = false; };
@@ -315,7 +334,7 @@ __device__ __forceinline__ bool plain_span(const StepParams &p, int xa, int xb, 
 //   q >= 1/2:  f*_opp(k)(x) / (2q) + (1 - 1/(2q)) f*_k(x),
 // and, when fxy is given, adds the link's momentum exchange (the population
 // that left along c_opp(k) plus the one that returns) to fxy.
-template <class S, class Fetch, bool INTERP = false>
+template <class S, class Fetch, bool INTERP = false, bool COH = false>
 __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &p, int xe, int y, uint32_t lm,
                                      Fetch fetch, typename Store<S>::C h[9], double *fxy = nullptr) {
   using C = typename Store<S>::C;
@@ -324,7 +343,7 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
   C drho_own = (C)0;
   if (p.bc == BC_MOVINGWALL && (y == 0 || y == p.ny - 1)) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) drho_own += Store<S>::ld(A[(size_t)k * p.plane + own]);
+    for (int k = 0; k < 9; ++k) drho_own += Store<S>::ld(own_ld<COH>(A + (size_t)k * p.plane + own));
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -338,11 +357,11 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
     }
     if (!inside) {
       if (CY(k) != 0 && p.bc == BC_MOVINGWALL && (unsigned)sy >= (unsigned)p.ny)
-        h[k] = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]) + (C)(6.0 * WD(k) * CX(k)) * U * drho_own;
+        h[k] = Store<S>::ld(own_ld<COH>(A + (size_t)OPP(k) * p.plane + own)) + (C)(6.0 * WD(k) * CX(k)) * U * drho_own;
       else
-        h[k] = Store<S>::ld(A[(size_t)k * p.plane + own]);
+        h[k] = Store<S>::ld(own_ld<COH>(A + (size_t)k * p.plane + own));
     } else if (lm & (1u << k)) {
-      const C hi = Store<S>::ld(A[(size_t)OPP(k) * p.plane + own]);
+      const C hi = Store<S>::ld(own_ld<COH>(A + (size_t)OPP(k) * p.plane + own));
       if constexpr (!INTERP) {
         h[k] = hi;
         if (CX(k) != 0) h[k] += (C)(-6.0 * WD(k) * CX(k)) * U;
@@ -357,7 +376,7 @@ __device__ __forceinline__ void pull(const S *__restrict__ A, const StepParams &
           wref = (C)1;
         } else {
           const C a = (C)(0.5f / q);
-          v = a * hi + ((C)1 - a) * Store<S>::ld(A[(size_t)k * p.plane + own]);
+          v = a * hi + ((C)1 - a) * Store<S>::ld(own_ld<COH>(A + (size_t)k * p.plane + own));
           wref = a;
         }
         if (CX(k) != 0) v += (C)(-6.0 * WD(k) * CX(k)) * U * wref;
@@ -649,10 +668,13 @@ __device__ __forceinline__ void link_force(const C h[9], uint32_t lm, double &fx
 
 // Final fixed-order reduction of the per-item force slots into history entry
 // step, executed by one full warp after every item of the step has posted.
-__device__ __forceinline__ void finish_force(const StepParams &p, int lane) {
-  double sx = 0.0, sy = 0.0;
-  for (int s = lane; s < p.nslots; s += 32) {
-    const double2 v = __ldcg(p.slots + s);
+// Sum of one step's force slots over a warp in a fixed order (each lane its
+// slots in index order, then a butterfly); the result is in every lane.
+__device__ __forceinline__ void slot_sum(const double2 *slots, int nslots, int lane, double &sx, double &sy) {
+  sx = 0.0;
+  sy = 0.0;
+  for (int s = lane; s < nslots; s += 32) {
+    const double2 v = __ldcg(slots + s);
     sx += v.x;
     sy += v.y;
   }
@@ -661,6 +683,11 @@ __device__ __forceinline__ void finish_force(const StepParams &p, int lane) {
     sx += __shfl_xor_sync(0xffffffffu, sx, o);
     sy += __shfl_xor_sync(0xffffffffu, sy, o);
   }
+}
+
+__device__ __forceinline__ void finish_force(const StepParams &p, int lane) {
+  double sx, sy;
+  slot_sum(p.slots, p.nslots, lane, sx, sy);
   if (lane == 0) {
     const unsigned long long n = *p.step;
     const long long r = (long long)(n % (unsigned long long)p.hist_cap);
@@ -737,6 +764,48 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 }
 __device__ __forceinline__ void named_bar(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// ---- multi-step kernel: per-CTA progress counters -------------------------
+// Steps [0, steps) of one launch; CTA b owns row tiles [b N / G, (b+1) N / G)
+// (N tiles, G CTAs) and, after finishing step s, publishes prog[b] = base +
+// s + 1 (release, GPU scope).  Before it loads the tiles of step s it waits
+// (acquire, GPU scope) until every CTA that owns a row within one row of its
+// own rows has published base + s: those CTAs wrote the rows it pulls from,
+// and have finished reading the rows it is about to overwrite.
+struct WaveParams {
+  unsigned *prog;   // [G] progress counters; the host never lets them exceed base
+  unsigned base;    // counter value of every CTA that finished the previous launch
+  int steps;        // steps of this launch
+  double2 *slots;   // [steps][nslots] force partial of every force tile and step
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Order the generic-proxy writes made visible by an acquire before the bulk
+// copies (async proxy) that read them.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Bounded wait until prog[c] >= target (modulo 2^32) for c in [c0, c1];
+// false after limit_ns (0: 1 s) or once another CTA reported a timeout.
+__device__ __forceinline__ bool wait_progress(const unsigned *prog, int c0, int c1, unsigned target,
+                                              const unsigned *err, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns(), lim = wait_limit(limit_ns);
+  for (int c = c0; c <= c1; ++c) {
+    while ((int)(ld_acquire_gpu(prog + c) - target) < 0) {
+      if (*(volatile const unsigned *)err & ERR_TIMEOUT) return false;
+      if (global_ns() - t0 > lim) return false;
+      __nanosleep(32);
+    }
+  }
+  return true;
 }
 
 }  // namespace gblbm

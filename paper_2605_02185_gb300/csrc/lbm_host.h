@@ -51,7 +51,7 @@ inline int check_opts(const lbm_opts *o) {
   if (!(o->U >= 0.0 && o->U < 0.3)) return LBM_ERR_ARG;
   if (o->bc_top_bottom < LBM_BC_FREESLIP || o->bc_top_bottom > LBM_BC_MOVINGWALL) return LBM_ERR_ARG;
   if (!elem_size(o->storage)) return LBM_ERR_ARG;
-  if (o->kernel < LBM_KERNEL_AUTO || o->kernel > LBM_KERNEL_TMA_BULK) return LBM_ERR_ARG;
+  if (o->kernel < LBM_KERNEL_AUTO || o->kernel > LBM_KERNEL_TMA_WAVE) return LBM_ERR_ARG;
   if (o->collision != LBM_COLLIDE_BGK && o->collision != LBM_COLLIDE_MRT) return LBM_ERR_ARG;
   if (o->collision == LBM_COLLIDE_MRT &&
       !(o->s_e > 0.0 && o->s_e < 2.0 && o->s_eps > 0.0 && o->s_eps < 2.0 && o->s_q > 0.0 && o->s_q < 2.0))

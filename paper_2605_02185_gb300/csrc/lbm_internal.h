@@ -9,6 +9,7 @@ namespace gblbm {
 
 struct StepParams;
 struct CaseDesc;
+struct WaveParams;
 
 // Launchers of one storage type.  All launches are asynchronous on `st`.
 struct KernelOps {
@@ -46,6 +47,13 @@ struct KernelOps {
   // shapes it is not built for
   cudaError_t (*tma_interp)(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st,
                             int prep);
+  // the multi-step TMA kernel (w.steps steps from A, then B, ... in one
+  // cooperative launch) and the reduction of its force slots into the
+  // history; shapes of GBLBM_WAVE_SHAPES (cudaErrorNotSupported otherwise)
+  cudaError_t (*wave)(int shape, int grid, void *A, void *B, const StepParams &p, const WaveParams &w,
+                      cudaStream_t st);
+  cudaError_t (*wave_prep)(int shape);
+  int (*wave_occupancy)(int shape);
 };
 
 // Look up (once per device) the address of lbm_step_noalloc's static
@@ -84,6 +92,14 @@ const KernelOps *ops_bf16sr();
   X(19, 13, 2, 3)           \
   X(20, 13, 2, 2)
 
+// Shapes (ids and triples of GBLBM_TMA_SHAPES) the multi-step kernel is
+// built for: the float defaults by lattice width and the 16-bit default.
+#define GBLBM_WAVE_SHAPES(X) \
+  X(6, 8, 2, 4)              \
+  X(12, 12, 2, 4)            \
+  X(15, 10, 2, 4)            \
+  X(19, 13, 2, 3)
+
 // Shapes of the TMA-load + TMA-bulk-store kernel X(id, warps, cells/thread, stages).
 #define GBLBM_TMA_BULK_SHAPES(X) \
   X(0, 12, 2, 4)                 \
@@ -99,6 +115,21 @@ struct TmaShape {
 constexpr TmaShape kTmaShapes[] = {GBLBM_TMA_SHAPES(GBLBM_SHAPE_ENTRY)};
 #undef GBLBM_SHAPE_ENTRY
 constexpr int kNumTmaShapes = (int)(sizeof(kTmaShapes) / sizeof(kTmaShapes[0]));
+#define GBLBM_WAVE_CHECK(id, a, b, c)                                                             \
+  static_assert(kTmaShapes[id].ncw == a && kTmaShapes[id].cpt == b && kTmaShapes[id].stages == c, \
+                "multi-step shape id does not match the TMA shape list");
+GBLBM_WAVE_SHAPES(GBLBM_WAVE_CHECK)
+#undef GBLBM_WAVE_CHECK
+#define GBLBM_SHAPE_ENTRY(id, a, b, c) {id, a, b, c},
+struct WaveShape {
+  int id, ncw, cpt, stages;
+};
+constexpr WaveShape kWaveShapes[] = {GBLBM_WAVE_SHAPES(GBLBM_SHAPE_ENTRY)};
+#undef GBLBM_SHAPE_ENTRY
+constexpr int kNumWaveShapes = (int)(sizeof(kWaveShapes) / sizeof(kWaveShapes[0]));
+// Steps per launch of the multi-step kernel and the most CTAs it runs with.
+constexpr int kWaveSteps = 64;
+constexpr int kWaveMaxGrid = 4096;
 #define GBLBM_SHAPE_ENTRY(id, a, b, c) {a, b, c},
 constexpr TmaShape kTmaBulkShapes[] = {GBLBM_TMA_BULK_SHAPES(GBLBM_SHAPE_ENTRY)};
 #undef GBLBM_SHAPE_ENTRY

@@ -10,12 +10,11 @@
 
 namespace gblbm {
 
-// Post one row tile's force partial to its slot; the tile that posts last in
-// the step reduces all slots (fixed order) into the history.  Called
-// uniformly by all nthr threads of the group; sync() is the group barrier.
+// One row tile's force partial summed over the group in a fixed order (each
+// warp's lanes, then the warps in order); the sum is valid in thread 0.
+// Called uniformly by all threads of the group; sync() is the group barrier.
 template <int NW, class Sync>
-__device__ __forceinline__ void post_force(const StepParams &p, int y, int s, double fx, double fy, int tid,
-                                           double (&red)[2][NW], int &s_last, Sync sync) {
+__device__ __forceinline__ double2 tile_force(double fx, double fy, int tid, double (&red)[2][NW], Sync sync) {
   const int warp = tid >> 5, lane = tid & 31;
   fx = warp_sum(fx);
   fy = warp_sum(fy);
@@ -24,15 +23,30 @@ __device__ __forceinline__ void post_force(const StepParams &p, int y, int s, do
     red[1][warp] = fy;
   }
   sync();
+  double sx = 0.0, sy = 0.0;
   if (tid == 0) {
-    double sx = 0.0, sy = 0.0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
       sx += red[0][w];
       sy += red[1][w];
     }
-    const int slot = (y - p.fy0) * (p.fs1 - p.fs0 + 1) + (s - p.fs0);
-    __stcg(p.slots + slot, make_double2(sx, sy));
+  }
+  return make_double2(sx, sy);
+}
+
+__device__ __forceinline__ int force_slot(const StepParams &p, int y, int s) {
+  return (y - p.fy0) * (p.fs1 - p.fs0 + 1) + (s - p.fs0);
+}
+
+// Post one row tile's force partial to its slot; the tile that posts last in
+// the step reduces all slots (fixed order) into the history.
+template <int NW, class Sync>
+__device__ __forceinline__ void post_force(const StepParams &p, int y, int s, double fx, double fy, int tid,
+                                           double (&red)[2][NW], int &s_last, Sync sync) {
+  const int warp = tid >> 5, lane = tid & 31;
+  const double2 sum = tile_force<NW>(fx, fy, tid, red, sync);
+  if (tid == 0) {
+    __stcg(p.slots + force_slot(p, y, s), sum);
     __threadfence();
     const unsigned prev = atomicAdd(p.done, 1u);
     s_last = (prev == (unsigned)(p.nslots - 1)) ? 1 : 0;
@@ -85,7 +99,7 @@ __device__ __forceinline__ bool collide_node(typename Store<S>::C (&h)[9], const
 // rules, collision into h; adds the node's links to the force.  With INTERP
 // (interpolated bounce-back) the links' momentum exchange is that of the
 // previous step, taken while pulling: it needs the returning populations.
-template <int MRT, class S, class Fetch, bool INTERP = false>
+template <int MRT, class S, class Fetch, bool INTERP = false, bool COH = false>
 __device__ __forceinline__ void node_compute(const S *__restrict__ A, const StepParams &p, int x, int y,
                                              const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
                                              bool &bad, typename Store<S>::C (&h)[9]) {
@@ -97,13 +111,13 @@ __device__ __forceinline__ void node_compute(const S *__restrict__ A, const Step
     for (int k = 0; k < 9; ++k) h[k] = (C)0;
   } else if constexpr (INTERP) {
     double fxy[2] = {0.0, 0.0};
-    pull<S, Fetch, true>(A, p, xe, y, lm, fetch, h, x == xe ? fxy : nullptr);
+    pull<S, Fetch, true, COH>(A, p, xe, y, lm, fetch, h, x == xe ? fxy : nullptr);
     fx += fxy[0];
     fy += fxy[1];
     boundaries<C>(h, xe, y, p);
     bad |= !collide_node<MRT, S>(h, cf);
   } else {
-    pull<S>(A, p, xe, y, lm, fetch, h);
+    pull<S, Fetch, false, COH>(A, p, xe, y, lm, fetch, h);
     boundaries<C>(h, xe, y, p);
     bad |= !collide_node<MRT, S>(h, cf);
     if ((lm & LM_LINKS) && x == xe) link_force<C>(h, lm, fx, fy);
@@ -134,12 +148,12 @@ __device__ __forceinline__ void store_node(S *__restrict__ B, const StepParams &
   }
 }
 
-template <int MRT, class S, class Fetch, bool INTERP = false>
+template <int MRT, class S, class Fetch, bool INTERP = false, bool COH = false>
 __device__ __forceinline__ void update_node(const S *__restrict__ A, S *__restrict__ B, const StepParams &p, int x,
                                             int y, const Coef<Lane<S>> &cf, Fetch fetch, double &fx, double &fy,
                                             bool &bad) {
   typename Store<S>::C h[9];
-  node_compute<MRT, S, Fetch, INTERP>(A, p, x, y, cf, fetch, fx, fy, bad, h);
+  node_compute<MRT, S, Fetch, INTERP, COH>(A, p, x, y, cf, fetch, fx, fy, bad, h);
   store_node<S>(B, p, x, y, h);
 }
 
@@ -155,7 +169,7 @@ __device__ __forceinline__ void update_plain(S *__restrict__ B, const StepParams
 // with bounce-back and placeholders, boundary rules, links): each node is
 // pulled on its own, the pair collides in the packed form the plain spans
 // use, so a node gets the same bits whichever span it falls in.
-template <int MRT, class S, class Fetch>
+template <int MRT, class S, class Fetch, bool COH = false>
 __device__ __forceinline__ void update_node_pair(const S *__restrict__ A, S *__restrict__ B, const StepParams &p,
                                                  int x, int y, const Coef<LF2> &cf2, Fetch fetch, double &fx,
                                                  double &fy, bool &bad) {
@@ -171,7 +185,7 @@ __device__ __forceinline__ void update_node_pair(const S *__restrict__ A, S *__r
 #pragma unroll
       for (int k = 0; k < 9; ++k) h[e][k] = 0.f;
     } else {
-      pull<S>(A, p, xe[e], y, lm[e], fetch, h[e]);
+      pull<S, Fetch, false, COH>(A, p, xe[e], y, lm[e], fetch, h[e]);
       boundaries<float>(h[e], xe[e], y, p);
     }
   }
@@ -396,6 +410,216 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
     if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+}
+
+// ---- multi-step TMA kernel ------------------------------------------------
+// The TMA kernel above run for w.steps steps in one cooperative launch.  CTA
+// b owns the contiguous row tiles [b N / G, (b+1) N / G) and runs them step
+// after step; before the loads of a step its producer waits only for the
+// CTAs that own a row within one row of its own (WaveParams), so the steps
+// are not separated by a launch boundary with its pipeline fill and tail.
+// Per node the arithmetic is that of step_tma, so the results are the same
+// bits; the node's own previous values are read through L2 (they were
+// written earlier in the launch), and each step's force partials go to a slot
+// row of their own, reduced in step order by wave_finish after the launch.
+template <class S, int NCW, int CPT, int STAGES, int MRT>
+__global__ void __launch_bounds__((NCW + 1) * 32)
+    step_tma_wave(S *buf0, S *buf1, StepParams p, WaveParams w) {
+  using C = typename Store<S>::C;
+  constexpr int PX = TmaPair<S>::nodes;
+  constexpr int H = 16 / (int)sizeof(S);
+  constexpr int NC = NCW * 32;
+  constexpr int W = NC * CPT * PX;
+  constexpr int SEG = W + 2 * H;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S *tiles = reinterpret_cast<S *>(smem);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
+  __shared__ double red[2][NCW];
+  __shared__ int s_abort_store;
+  volatile int *s_abort = &s_abort_store;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nitems = (long long)p.ny * p.nseg;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int i0 = (int)((long long)b * nitems / G), i1 = (int)((long long)(b + 1) * nitems / G);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) {
+      mbar_init(smem_addr(&bars[q]), 1);
+      mbar_init(smem_addr(&bars[STAGES + q]), NCW);
+    }
+    *s_abort = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NCW) {  // ---------------- producer
+    if (lane == 0) {
+      // CTAs that own rows [y0 - 1, y1 + 1] (wrapped when periodic): at most
+      // three ranges of consecutive CTAs, this one among them
+      auto owner = [&](long long i) { return (int)(((i + 1) * G - 1) / nitems); };
+      int dep[3][2], nd = 0;
+      int ylo = i0 / p.nseg - 1, yhi = (i1 - 1) / p.nseg + 1;
+      if (p.bc == BC_PERIODIC) {
+        if (ylo < 0) {
+          dep[nd][0] = owner((long long)(p.ny - 1) * p.nseg);
+          dep[nd++][1] = G - 1;
+          ylo = 0;
+        }
+        if (yhi >= p.ny) {
+          dep[nd][0] = 0;
+          dep[nd++][1] = owner((long long)p.nseg - 1);
+          yhi = p.ny - 1;
+        }
+      } else {
+        ylo = max(ylo, 0);
+        yhi = min(yhi, p.ny - 1);
+      }
+      dep[nd][0] = owner((long long)ylo * p.nseg);
+      dep[nd++][1] = owner((long long)(yhi + 1) * p.nseg - 1);
+
+      int j = 0;
+      bool stop = false;
+      for (int s = 0; s < w.steps && !stop; ++s) {
+        const S *A = (s & 1) ? buf1 : buf0;
+        if (s > 0) {
+          bool ok = true;
+          for (int d = 0; d < nd && ok; ++d)
+            ok = wait_progress(w.prog, dep[d][0], dep[d][1], w.base + (unsigned)s, p.err, p.wait_ns);
+          if (!ok) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            *s_abort = 1;
+            break;
+          }
+          fence_proxy_async_global();
+        }
+        for (int t = i0; t < i1; ++t, ++j) {
+          const int st = j % STAGES;
+          if (j >= STAGES &&
+              !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
+            if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
+            *s_abort = 1;
+            stop = true;
+            break;
+          }
+          if (*s_abort) {
+            stop = true;
+            break;
+          }
+          const int y = t / p.nseg, sg = t - y * p.nseg;
+          const int x0 = sg * W;
+          const int xs = max(x0 - H, 0), xl = min(x0 + W + H, p.pitch);
+          const uint32_t bytes = (uint32_t)(xl - xs) * (uint32_t)sizeof(S);
+          int rows[9];
+          uint32_t total = 0;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            int sy = y - CY(k);
+            if (p.bc == BC_PERIODIC) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+            rows[k] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
+            total += rows[k] >= 0 ? bytes : 0u;
+          }
+          const uint32_t fb = smem_addr(&bars[st]);
+          mbar_arrive_expect_tx(fb, total);
+          if (t == p.fault_tile) continue;  // failure-path test: announced, never copied
+          S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            if (rows[k] >= 0)
+              bulk_g2s(smem_addr(dst + (size_t)k * SEG), A + (size_t)k * p.plane + (size_t)rows[k] * p.pitch + xs,
+                       bytes, fb);
+        }
+      }
+      // Do not leave while a copy into this CTA's shared memory is in flight.
+      for (int q = max(0, j - STAGES); q < j; ++q) {
+        const uint32_t fb = smem_addr(&bars[q % STAGES]);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
+          if (global_ns() - t0 > wait_limit(p.wait_ns)) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            break;
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------------- compute warps
+  const int ctid = threadIdx.x;
+  const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
+  const Coef<LF2> cf2 = make_coef<LF2>(p);
+  bool bad = false;
+  int j = 0;
+  for (int s = 0; s < w.steps; ++s) {
+    const S *A = (s & 1) ? buf1 : buf0;
+    S *B = (s & 1) ? buf0 : buf1;
+    double2 *slots = w.slots + (size_t)s * p.nslots;
+    for (int t = i0; t < i1; ++t, ++j) {
+      const int st = j % STAGES;
+      bool ok = false;
+      if (!*s_abort) {
+        ok = mbar_wait_bounded(smem_addr(&bars[st]), (j / STAGES) & 1, s_abort, p.wait_ns);
+        if (!ok && !*s_abort) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          *s_abort = 1;
+        }
+      }
+      const int y = t / p.nseg, sg = t - y * p.nseg;
+      const int x0 = sg * W;
+      double fx = 0.0, fy = 0.0;
+      if (ok) {
+        const S *tile = tiles + (size_t)st * 9 * SEG + (H - x0);
+        auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int xw = x0 + (c * NC + (ctid & ~31)) * PX;
+          if constexpr (PX == 2) {
+            const int x = xw + 2 * lane;
+            if (plain_span(p, xw, xw + 63, y))
+              update_pair<MRT, S>(B, p, x, y, cf2, tile, SEG, bad);
+            else if (x < p.nx)
+              update_node_pair<MRT, S, decltype(fetch), true>(A, B, p, x, y, cf2, fetch, fx, fy, bad);
+          } else {
+            const int x = xw + lane;
+            if (plain_span(p, xw, xw + 31, y))
+              update_plain<MRT, S>(B, p, x, y, cf, fetch, bad);
+            else if (x < p.nx)
+              update_node<MRT, S, decltype(fetch), false, true>(A, B, p, x, y, cf, fetch, fx, fy, bad);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
+      }
+      if (is_force_item(p, y, sg)) {
+        const double2 sum = tile_force<NCW>(fx, fy, ctid, red, [] { named_bar(1, NC); });
+        if (ctid == 0) __stcg(slots + force_slot(p, y, sg), sum);
+        named_bar(1, NC);
+      }
+    }
+    // every compute thread's stores of step s, then the release of the counter
+    named_bar(2, NC);
+    if (ctid == 0) st_release_gpu(w.prog + b, w.base + (unsigned)s + 1u);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+}
+
+// History entries of a multi-step launch: each step's slots reduced as
+// finish_force reduces them, written in step order.
+template <class S>
+__global__ void __launch_bounds__(1024) wave_finish(StepParams p, WaveParams w) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long n0 = *p.step;
+  for (int s = warp; s < w.steps; s += 32) {
+    double sx, sy;
+    slot_sum(w.slots + (size_t)s * p.nslots, p.nslots, lane, sx, sy);
+    if (lane == 0) {
+      const long long r = (long long)((n0 + (unsigned long long)s) % (unsigned long long)p.hist_cap);
+      p.hist[2 * r] = sx + p.fconst_x;
+      p.hist[2 * r + 1] = sy + p.fconst_y;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *p.step = n0 + (unsigned long long)w.steps;
 }
 
 // Case of batch-wide row tile t: the last case whose first tile is <= t.
@@ -1018,6 +1242,68 @@ struct Launch {
     return cudaErrorNotSupported;
   }
 
+  // The multi-step kernel (cooperative launch, so that all CTAs are
+  // resident at once) followed by the reduction of its force slots.
+  template <int NCW, int CPT, int STAGES>
+  static cudaError_t wave_one(int grid, void *A, void *B, const StepParams &p, const WaveParams &w, cudaStream_t st,
+                              int mode, int *occ) {
+    constexpr size_t smem = tma_smem_bytes<S, NCW, CPT, STAGES, TmaPair<S>::nodes>();
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    auto k0 = step_tma_wave<S, NCW, CPT, STAGES, 0>;
+    auto k1 = step_tma_wave<S, NCW, CPT, STAGES, 1>;
+    if (mode == 1) {  // set the shared-memory limit
+      const cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (mode == 2) {  // resident CTAs per SM into *occ
+      int n = 0, m = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k0, (NCW + 1) * 32, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k1, (NCW + 1) * 32, smem) != cudaSuccess)
+        return cudaErrorInvalidConfiguration;
+      *occ = n < m ? n : m;
+      return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((NCW + 1) * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = p.mrt ? cudaLaunchKernelEx(&cfg, k1, (S *)A, (S *)B, p, w)
+                                : cudaLaunchKernelEx(&cfg, k0, (S *)A, (S *)B, p, w);
+    if (e != cudaSuccess) return e;
+    wave_finish<S><<<1, 1024, 0, st>>>(p, w);
+    return cudaGetLastError();
+  }
+  static cudaError_t wave_dispatch(int shape, int grid, void *A, void *B, const StepParams &p, const WaveParams &w,
+                                   cudaStream_t st, int mode, int *occ) {
+    switch (shape) {
+#define X(id, a, b, c) \
+  case id:             \
+    return wave_one<a, b, c>(grid, A, B, p, w, st, mode, occ);
+      GBLBM_WAVE_SHAPES(X)
+#undef X
+    }
+    return cudaErrorNotSupported;
+  }
+  static cudaError_t wave(int shape, int grid, void *A, void *B, const StepParams &p, const WaveParams &w,
+                          cudaStream_t st) {
+    return wave_dispatch(shape, grid, A, B, p, w, st, 0, nullptr);
+  }
+  static cudaError_t wave_prep(int shape) {
+    return wave_dispatch(shape, 0, nullptr, nullptr, StepParams{}, WaveParams{}, nullptr, 1, nullptr);
+  }
+  static int wave_occupancy(int shape) {
+    int n = 0;
+    if (wave_dispatch(shape, 0, nullptr, nullptr, StepParams{}, WaveParams{}, nullptr, 2, &n) != cudaSuccess) return 0;
+    return n;
+  }
+
   static cudaError_t tma(int shape, int grid, const void *A, void *B, const StepParams &p, cudaStream_t st) {
     switch (shape) {
 #define X(id, a, b, c) \
@@ -1223,7 +1509,7 @@ struct Launch {
                                   &smem,          &init,       &force,        &fields,   &mass_rows,
                                   &batch_direct,  &batch_tma,  &batch_prep, &init_device,
                                   &tma_bulk,      &bulk_prep,  &bulk_occupancy, &bulk_smem,
-                                  TmaPair<S>::nodes, &tma_interp};
+                                  TmaPair<S>::nodes, &tma_interp, &wave,  &wave_prep, &wave_occupancy};
     return &ops;
   }
 };

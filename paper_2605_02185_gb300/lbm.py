@@ -24,7 +24,7 @@ LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT = -1, -2, -3, -4
 LBM_ERR_OOM, LBM_ERR_RANGE, LBM_ERR_STATE = -5, -6, -7
 LBM_BC_FREESLIP, LBM_BC_PERIODIC, LBM_BC_ZOUHE, LBM_BC_MOVINGWALL = 0, 1, 2, 3
 LBM_F32, LBM_F16_OFS, LBM_BF16_OFS, LBM_F64, LBM_F16_SR, LBM_BF16_SR = 0, 1, 2, 3, 4, 5
-LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK = 0, 1, 2, 3
+LBM_KERNEL_AUTO, LBM_KERNEL_DIRECT, LBM_KERNEL_TMA, LBM_KERNEL_TMA_BULK, LBM_KERNEL_TMA_WAVE = 0, 1, 2, 3, 4
 LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
 LBM_BOUNCE_HALFWAY, LBM_BOUNCE_INTERPOLATED = 0, 1
 ELEM_BYTES = {LBM_F32: 4, LBM_F16_OFS: 2, LBM_BF16_OFS: 2, LBM_F64: 8, LBM_F16_SR: 2, LBM_BF16_SR: 2}

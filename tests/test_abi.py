@@ -60,6 +60,10 @@ def test_host_only_entry_points(lib):
     assert b >= 2 * 9 * 200 * 448 * 4
     o.storage = lbm.LBM_F16_OFS
     assert lbm.lbm_workspace_bytes(o, mask) < b
+    # the multi-step kernel is built for four of the TMA kernel's shapes
+    wave = lbm.lbm_kernel_shapes(lbm.LBM_KERNEL_TMA_WAVE)
+    assert wave == [(8, 2, 4), (12, 2, 4), (10, 2, 4), (13, 2, 3)]
+    assert set(wave) <= set(lbm.lbm_kernel_shapes(lbm.LBM_KERNEL_TMA))
 
 
 @pytest.mark.parametrize("bad", [
