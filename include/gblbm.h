@@ -80,16 +80,18 @@ extern "C" {
                                  (single lattices; not for batches) */
 #define LBM_KERNEL_TMA_WAVE 4 /* the TMA kernel run for up to 64 steps per launch
                                  (single lattices; not for batches): a cooperative
-                                 launch in which each CTA owns a contiguous band of
-                                 row tiles and, between steps, waits (bounded) only
-                                 for the CTAs whose rows border its own, so steps
-                                 are not separated by a launch, its pipeline fill
-                                 and its tail.  Results are bit-identical to
-                                 LBM_KERNEL_TMA.  Built for the shapes that
-                                 lbm_kernel_shapes_for lists; half-way
-                                 bounce-back only (interpolated bounce-back runs
-                                 on the kernels named under lbm_opts.bounce).
-                                 No CUDA graph is captured for it. */
+                                 launch in which a row tile of step s starts as
+                                 soon as the tiles of its own and the two
+                                 neighbouring rows have finished step s - 1
+                                 (per-row completion counters, bounded waits),
+                                 so steps are not separated by a launch, its
+                                 pipeline fill and its tail.  Results are
+                                 bit-identical to LBM_KERNEL_TMA.  Built for the
+                                 shapes that lbm_kernel_shapes_for lists;
+                                 half-way bounce-back only (interpolated
+                                 bounce-back runs on the kernels named under
+                                 lbm_opts.bounce).  No CUDA graph is captured
+                                 for it. */
 
 typedef struct lbm_ctx lbm_ctx;
 

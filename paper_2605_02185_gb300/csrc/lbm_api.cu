@@ -38,7 +38,7 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   const size_t hist = align_up((size_t)cap * 2 * sizeof(double), kAlign);
   const size_t ctrl = kAlign;
   const size_t wave_slots = align_up((size_t)kWaveSteps * slot_cap * sizeof(double2), kAlign);
-  const size_t wave_prog = align_up((size_t)kWaveMaxGrid * sizeof(unsigned), kAlign);
+  const size_t wave_rows = align_up((size_t)o->ny * sizeof(unsigned), kAlign);
   const int band_rows = (int)std::max<size_t>(1, std::min<size_t>((size_t)o->ny, kBandCells / (size_t)o->nx));
   const size_t staging =
       align_up(std::max<size_t>((size_t)band_rows * o->nx * 3 * sizeof(double), (size_t)o->ny * sizeof(double)), kAlign);
@@ -51,7 +51,7 @@ size_t layout(const lbm_opts *o, const Geometry &g, int *pitch_out, size_t offs[
   offs[5] = off; off += ctrl;
   offs[6] = off; off += staging;
   offs[7] = off; off += wave_slots;
-  offs[8] = off; off += wave_prog;
+  offs[8] = off; off += wave_rows;
   offs[9] = off;
   *pitch_out = pitch;
   *slot_cap_out = slot_cap;
@@ -128,9 +128,8 @@ int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
   const int grid = kernel == LBM_KERNEL_DIRECT ? (int)nitems
                                                : (int)std::min<long long>(nitems, (long long)c->sms * ctas_per_sm);
   if (kernel == LBM_KERNEL_TMA_WAVE) {
-    if (grid > kWaveMaxGrid) return LBM_ERR_ARG;
-    // a new grid starts from cleared progress counters
-    CK(cudaMemsetAsync(c->wave_prog, 0, (size_t)kWaveMaxGrid * sizeof(unsigned), c->stream));
+    // a new tiling starts from cleared row counters
+    CK(cudaMemsetAsync(c->wave_rows, 0, (size_t)c->ny * sizeof(unsigned), c->stream));
     c->wave_base = 0;
   }
   c->kernel = kernel;
@@ -151,16 +150,24 @@ cudaError_t launch_step(lbm_ctx *c, int from) {
   return c->ops->tma(c->shape, c->grid, A, B, c->p, c->stream);
 }
 
+// Clear the multi-step kernel's row counters (a new state, or the recovery
+// from a launch that gave up and left them uneven).
+cudaError_t reset_wave_rows(lbm_ctx *c) {
+  c->wave_base = 0;
+  return cudaMemsetAsync(c->wave_rows, 0, (size_t)c->ny * sizeof(unsigned), c->stream);
+}
+
 // Steps [0, n) on the multi-step kernel, kWaveSteps per launch.
 int wave_steps(lbm_ctx *c, int64_t n) {
   while (n > 0) {
     const int k = (int)std::min<int64_t>(n, kWaveSteps);
-    if (c->wave_base > (1u << 30)) {  // keep counter differences far from 2^31
-      CK(cudaMemsetAsync(c->wave_prog, 0, (size_t)kWaveMaxGrid * sizeof(unsigned), c->stream));
+    if ((unsigned long long)(c->wave_base + k) * (unsigned)c->nseg > (1ull << 30)) {
+      // keep the counters and their differences far from 2^31
+      CK(cudaMemsetAsync(c->wave_rows, 0, (size_t)c->ny * sizeof(unsigned), c->stream));
       c->wave_base = 0;
     }
     WaveParams w;
-    w.prog = c->wave_prog;
+    w.rows_done = c->wave_rows;
     w.base = c->wave_base;
     w.steps = k;
     w.slots = c->wave_slots;
@@ -288,7 +295,7 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   c->staging = base + offs[6];
   c->staging_bytes = offs[7] - offs[6];
   c->wave_slots = (double2 *)(base + offs[7]);
-  c->wave_prog = (unsigned *)(base + offs[8]);
+  c->wave_rows = (unsigned *)(base + offs[8]);
   if (o->stream) {
     c->stream = (cudaStream_t)o->stream;
   } else {
@@ -392,6 +399,7 @@ int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u, const double
     CK(c->ops->init(c->buf[0], c->p, sr, su, sv, y0, rows, c->stream));
   }
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
+  CK(reset_wave_rows(c));
   CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
   if (!c->qmap) CK(c->ops->force(c->buf[0], c->p, c->stream));  // interpolated: F(0) comes with step 1
   CK(cudaStreamSynchronize(c->stream));
@@ -405,6 +413,7 @@ int lbm_init_fields_device(lbm_ctx *c, const float *rho, const float *u, const f
   c->cur = 0;
   CK(c->ops->init_device(c->buf[0], c->p, rho, u, v, with_noneq ? 1 : 0, 1.0 / c->p.omega, c->stream));
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
+  CK(reset_wave_rows(c));
   CK(cudaMemsetAsync(c->buf[1], 0, (size_t)9 * c->plane * c->elem, c->stream));
   if (!c->qmap) CK(c->ops->force(c->buf[0], c->p, c->stream));  // interpolated: F(0) comes with step 1
   CK(cudaStreamSynchronize(c->stream));
@@ -559,6 +568,7 @@ int lbm_set_populations(lbm_ctx *c, const void *src, size_t bytes, int64_t step)
   CK(cudaMemcpy2DAsync(c->buf[0], (size_t)c->pitch * c->elem, src, w, w, (size_t)9 * c->ny, cudaMemcpyHostToDevice,
                        c->stream));
   CK(cudaMemsetAsync(c->ctrl, 0, kAlign, c->stream));
+  CK(reset_wave_rows(c));
   const unsigned long long s = (unsigned long long)step;
   CK(cudaMemcpyAsync(c->ctrl + 2, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));

@@ -58,9 +58,9 @@ struct lbm_ctx {
   gblbm::StepParams p{};
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
-  // multi-step kernel: per-CTA progress counters, their value after the
-  // last launch, and the force slots of one launch's steps
-  unsigned *wave_prog = nullptr;
+  // multi-step kernel: per-row completion counters, the steps they have
+  // counted, and the force slots of one launch's steps
+  unsigned *wave_rows = nullptr;
   unsigned wave_base = 0;
   double2 *wave_slots = nullptr;
 };

@@ -222,7 +222,9 @@ template <> struct Dithers<half_sr> { static constexpr bool value = true; };
 template <> struct Dithers<bf16_sr> { static constexpr bool value = true; };
 
 // ---- per-step parameters (passed by value) -------------------------------
-struct StepParams {
+// 16-byte aligned and sized so that the batched kernel can stage a case's
+// parameters into shared memory with one bulk copy.
+struct alignas(16) StepParams {
   int nx, ny, pitch, bc;
   long long plane;         // elements per population plane
   double omega;            // 1 / tau
@@ -295,7 +297,7 @@ __host__ __device__ inline void fill_coefs(StepParams &p) {
 // (buf[parity] holds f*(n)) and the index of its first row tile in the
 // batch-wide tile numbering.
 struct CaseDesc {
-  StepParams p;
+  StepParams p;  // first: 16-byte aligned in an array of descriptors
   const void *buf[2];
   long long item0;
 };
@@ -719,6 +721,18 @@ __device__ __forceinline__ void mbar_fence_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// Non-blocking test: true when the phase with this parity has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -766,46 +780,33 @@ __device__ __forceinline__ void named_bar(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// ---- multi-step kernel: per-CTA progress counters -------------------------
-// Steps [0, steps) of one launch; CTA b owns row tiles [b N / G, (b+1) N / G)
-// (N tiles, G CTAs) and, after finishing step s, publishes prog[b] = base +
-// s + 1 (release, GPU scope).  Before it loads the tiles of step s it waits
-// (acquire, GPU scope) until every CTA that owns a row within one row of its
-// own rows has published base + s: those CTAs wrote the rows it pulls from,
-// and have finished reading the rows it is about to overwrite.
+// ---- multi-step kernel: per-row completion counters ------------------------
+// rows_done[y] counts the row tiles of row y that finished a step, over the
+// launches since the counters were last cleared: when a launch starts, every
+// row stands at base * nseg (base = steps run since then); step s of the
+// launch is complete for row y once rows_done[y] reaches (base + s + 1) * nseg.
 struct WaveParams {
-  unsigned *prog;   // [G] progress counters; the host never lets them exceed base
-  unsigned base;    // counter value of every CTA that finished the previous launch
-  int steps;        // steps of this launch
-  double2 *slots;   // [steps][nslots] force partial of every force tile and step
+  unsigned *rows_done;  // [ny]
+  unsigned base;        // steps run since the counters were cleared
+  int steps;            // steps of this launch
+  double2 *slots;       // [steps][nslots] force partial of every force tile and step
 };
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
   unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_relaxed_gpu_add(unsigned *p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// With relaxed loads before it, an acquire; with relaxed writes after it, a
+// release (GPU scope).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // Order the generic-proxy writes made visible by an acquire before the bulk
 // copies (async proxy) that read them.
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-// Bounded wait until prog[c] >= target (modulo 2^32) for c in [c0, c1];
-// false after limit_ns (0: 1 s) or once another CTA reported a timeout.
-__device__ __forceinline__ bool wait_progress(const unsigned *prog, int c0, int c1, unsigned target,
-                                              const unsigned *err, unsigned long long limit_ns) {
-  const unsigned long long t0 = global_ns(), lim = wait_limit(limit_ns);
-  for (int c = c0; c <= c1; ++c) {
-    while ((int)(ld_acquire_gpu(prog + c) - target) < 0) {
-      if (*(volatile const unsigned *)err & ERR_TIMEOUT) return false;
-      if (global_ns() - t0 > lim) return false;
-      __nanosleep(32);
-    }
-  }
-  return true;
 }
 
 }  // namespace gblbm

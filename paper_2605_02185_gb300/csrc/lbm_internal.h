@@ -127,9 +127,8 @@ struct WaveShape {
 constexpr WaveShape kWaveShapes[] = {GBLBM_WAVE_SHAPES(GBLBM_SHAPE_ENTRY)};
 #undef GBLBM_SHAPE_ENTRY
 constexpr int kNumWaveShapes = (int)(sizeof(kWaveShapes) / sizeof(kWaveShapes[0]));
-// Steps per launch of the multi-step kernel and the most CTAs it runs with.
+// Steps per launch of the multi-step kernel.
 constexpr int kWaveSteps = 64;
-constexpr int kWaveMaxGrid = 4096;
 #define GBLBM_SHAPE_ENTRY(id, a, b, c) {a, b, c},
 constexpr TmaShape kTmaBulkShapes[] = {GBLBM_TMA_BULK_SHAPES(GBLBM_SHAPE_ENTRY)};
 #undef GBLBM_SHAPE_ENTRY

@@ -413,17 +413,45 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
 }
 
 // ---- multi-step TMA kernel ------------------------------------------------
-// The TMA kernel above run for w.steps steps in one cooperative launch.  CTA
-// b owns the contiguous row tiles [b N / G, (b+1) N / G) and runs them step
-// after step; before the loads of a step its producer waits only for the
-// CTAs that own a row within one row of its own (WaveParams), so the steps
-// are not separated by a launch boundary with its pipeline fill and tail.
+// The TMA kernel above run for w.steps steps in one cooperative launch, with
+// the same grid-stride order of row tiles in every step (so the work of the
+// boundary rows and of the body is spread over all CTAs as in step_tma).
+// The launch boundary between steps is replaced by per-row completion
+// counters: the producer loads a tile of row y for step s only after every
+// tile of rows y - 1, y, y + 1 has finished step s - 1 (they wrote the rows
+// it pulls, and have read the rows it will overwrite).  A CTA can therefore
+// start the next step's first rows while other CTAs finish the last rows of
+// the step before: no pipeline fill and no tail per step.
+// CTA = NCW compute warps, the producer warp, and a publisher warp that
+// waits for each tile's "done" mbarrier (all compute warps finished it), adds
+// the tile to its row's counter (a batch of tiles per GPU-scope fence) and
+// then frees the stage on a third mbarrier, the one the producer waits on
+// before it reuses the stage: producer, compute warps and publisher so stay
+// within one phase of each other on every stage, which the parity waits
+// need.  The publisher depends on nothing but this CTA's compute warps, so a
+// producer waiting on a counter never holds back a completion another CTA
+// waits for.  The producer checks the rows of the next WAVE_AHEAD tiles with
+// one round of independent loads.
 // Per node the arithmetic is that of step_tma, so the results are the same
 // bits; the node's own previous values are read through L2 (they were
 // written earlier in the launch), and each step's force partials go to a slot
 // row of their own, reduced in step order by wave_finish after the launch.
+constexpr int WAVE_AHEAD = 8;
+
+// Rows a tile of row y pulls from: y - 1 .. y + 1, wrapped (periodic) or
+// clipped to the lattice.
+__device__ __forceinline__ void wave_rows(const StepParams &p, int y, int (&r)[3], int &n) {
+  n = 0;
+  for (int d = -1; d <= 1; ++d) {
+    int yy = y + d;
+    if (p.bc == BC_PERIODIC) yy = yy < 0 ? yy + p.ny : (yy >= p.ny ? yy - p.ny : yy);
+    else if (yy < 0 || yy >= p.ny) continue;
+    r[n++] = yy;
+  }
+}
+
 template <class S, int NCW, int CPT, int STAGES, int MRT>
-__global__ void __launch_bounds__((NCW + 1) * 32)
+__global__ void __launch_bounds__((NCW + 2) * 32)
     step_tma_wave(S *buf0, S *buf1, StepParams p, WaveParams w) {
   using C = typename Store<S>::C;
   constexpr int PX = TmaPair<S>::nodes;
@@ -434,68 +462,67 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
   extern __shared__ __align__(128) unsigned char smem[];
   S *tiles = reinterpret_cast<S *>(smem);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
+  __shared__ uint64_t freed[STAGES];  // publisher -> producer: stage free again
   __shared__ double red[2][NCW];
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long nitems = (long long)p.ny * p.nseg;
-  const int G = gridDim.x, b = blockIdx.x;
-  const int i0 = (int)((long long)b * nitems / G), i1 = (int)((long long)(b + 1) * nitems / G);
+  const int nitems = p.ny * p.nseg;
+  const int G = gridDim.x;
+  const int per_step = (nitems - (int)blockIdx.x + G - 1) / G;  // tiles of this CTA in a step (G <= nitems)
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) {
       mbar_init(smem_addr(&bars[q]), 1);
       mbar_init(smem_addr(&bars[STAGES + q]), NCW);
+      mbar_init(smem_addr(&freed[q]), 1);
     }
     *s_abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
 
+  if (warp == NCW + 1) {  // ---------------- publisher
+    if (lane == 0) {
+      const long long total = (long long)per_step * w.steps;
+      long long q = 0;
+      int k = 0;  // in-step index of tile q
+      while (q < total) {
+        if (!mbar_wait_bounded(smem_addr(&bars[STAGES + (int)(q % STAGES)]), (unsigned)((q / STAGES) & 1), s_abort,
+                               p.wait_ns)) {
+          if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
+          *s_abort = 1;
+          break;
+        }
+        int n = 1;  // and every later tile already done, without waiting
+        while (n < STAGES && q + n < total &&
+               mbar_test_wait(smem_addr(&bars[STAGES + (int)((q + n) % STAGES)]), (unsigned)(((q + n) / STAGES) & 1)))
+          ++n;
+        fence_acq_rel_gpu();
+        for (int i = 0; i < n; ++i) {
+          const int y = ((int)blockIdx.x + k * G) / p.nseg;
+          red_relaxed_gpu_add(w.rows_done + y, 1u);
+          if (++k == per_step) k = 0;
+        }
+        for (int i = 0; i < n; ++i) mbar_arrive(smem_addr(&freed[(int)((q + i) % STAGES)]));
+        q += n;
+      }
+    }
+    return;
+  }
+
   if (warp == NCW) {  // ---------------- producer
     if (lane == 0) {
-      // CTAs that own rows [y0 - 1, y1 + 1] (wrapped when periodic): at most
-      // three ranges of consecutive CTAs, this one among them
-      auto owner = [&](long long i) { return (int)(((i + 1) * G - 1) / nitems); };
-      int dep[3][2], nd = 0;
-      int ylo = i0 / p.nseg - 1, yhi = (i1 - 1) / p.nseg + 1;
-      if (p.bc == BC_PERIODIC) {
-        if (ylo < 0) {
-          dep[nd][0] = owner((long long)(p.ny - 1) * p.nseg);
-          dep[nd++][1] = G - 1;
-          ylo = 0;
-        }
-        if (yhi >= p.ny) {
-          dep[nd][0] = 0;
-          dep[nd++][1] = owner((long long)p.nseg - 1);
-          yhi = p.ny - 1;
-        }
-      } else {
-        ylo = max(ylo, 0);
-        yhi = min(yhi, p.ny - 1);
-      }
-      dep[nd][0] = owner((long long)ylo * p.nseg);
-      dep[nd++][1] = owner((long long)(yhi + 1) * p.nseg - 1);
-
-      int j = 0;
+      int j = 0;  // tiles issued (all steps of this launch)
       bool stop = false;
       for (int s = 0; s < w.steps && !stop; ++s) {
         const S *A = (s & 1) ? buf1 : buf0;
-        if (s > 0) {
-          bool ok = true;
-          for (int d = 0; d < nd && ok; ++d)
-            ok = wait_progress(w.prog, dep[d][0], dep[d][1], w.base + (unsigned)s, p.err, p.wait_ns);
-          if (!ok) {
-            atomicOr(p.err, ERR_TIMEOUT);
-            *s_abort = 1;
-            break;
-          }
-          fence_proxy_async_global();
-        }
-        for (int t = i0; t < i1; ++t, ++j) {
+        const unsigned need = (w.base + (unsigned)s) * (unsigned)p.nseg;  // step s - 1 done
+        int ver = s > 0 ? 0 : per_step;  // in-step tiles [0, ver) have their rows checked
+        int k = 0;
+        for (int t = blockIdx.x; t < nitems; t += G, ++j, ++k) {
           const int st = j % STAGES;
-          if (j >= STAGES &&
-              !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
+          if (j >= STAGES && !mbar_wait_bounded(smem_addr(&freed[st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
             if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
             *s_abort = 1;
             stop = true;
@@ -505,6 +532,38 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
             stop = true;
             break;
           }
+          if (k >= ver) {  // rows of tiles k .. k + WAVE_AHEAD - 1 of step s - 1
+            const unsigned long long t0 = global_ns(), lim = wait_limit(p.wait_ns);
+            while (true) {
+              unsigned v[WAVE_AHEAD][3];
+              int nr[WAVE_AHEAD];
+#pragma unroll
+              for (int i = 0; i < WAVE_AHEAD; ++i) {
+                int r[3];
+                nr[i] = 0;
+                if (k + i < per_step) wave_rows(p, (t + i * G) / p.nseg, r, nr[i]);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) v[i][e] = e < nr[i] ? ld_relaxed_gpu(w.rows_done + r[e]) : need;
+              }
+              int m = 0;
+              while (m < WAVE_AHEAD && k + m < per_step && (int)(v[m][0] - need) >= 0 && (int)(v[m][1] - need) >= 0 &&
+                     (int)(v[m][2] - need) >= 0)
+                ++m;
+              if (m > 0) {
+                ver = k + m;
+                break;
+              }
+              if ((*(volatile const unsigned *)p.err & ERR_TIMEOUT) || global_ns() - t0 > lim) break;
+            }
+            if (k >= ver) {
+              atomicOr(p.err, ERR_TIMEOUT);
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            fence_acq_rel_gpu();  // the loads above become an acquire
+            fence_proxy_async_global();
+          }
           const int y = t / p.nseg, sg = t - y * p.nseg;
           const int x0 = sg * W;
           const int xs = max(x0 - H, 0), xl = min(x0 + W + H, p.pitch);
@@ -512,20 +571,20 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
           int rows[9];
           uint32_t total = 0;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            int sy = y - CY(k);
+          for (int kk = 0; kk < 9; ++kk) {
+            int sy = y - CY(kk);
             if (p.bc == BC_PERIODIC) sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-            rows[k] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
-            total += rows[k] >= 0 ? bytes : 0u;
+            rows[kk] = ((unsigned)sy < (unsigned)p.ny) ? sy : -1;
+            total += rows[kk] >= 0 ? bytes : 0u;
           }
           const uint32_t fb = smem_addr(&bars[st]);
           mbar_arrive_expect_tx(fb, total);
           if (t == p.fault_tile) continue;  // failure-path test: announced, never copied
           S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
-          for (int k = 0; k < 9; ++k)
-            if (rows[k] >= 0)
-              bulk_g2s(smem_addr(dst + (size_t)k * SEG), A + (size_t)k * p.plane + (size_t)rows[k] * p.pitch + xs,
+          for (int kk = 0; kk < 9; ++kk)
+            if (rows[kk] >= 0)
+              bulk_g2s(smem_addr(dst + (size_t)kk * SEG), A + (size_t)kk * p.plane + (size_t)rows[kk] * p.pitch + xs,
                        bytes, fb);
         }
       }
@@ -554,7 +613,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
     const S *A = (s & 1) ? buf1 : buf0;
     S *B = (s & 1) ? buf0 : buf1;
     double2 *slots = w.slots + (size_t)s * p.nslots;
-    for (int t = i0; t < i1; ++t, ++j) {
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x, ++j) {
       const int st = j % STAGES;
       bool ok = false;
       if (!*s_abort) {
@@ -596,9 +655,6 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         named_bar(1, NC);
       }
     }
-    // every compute thread's stores of step s, then the release of the counter
-    named_bar(2, NC);
-    if (ctid == 0) st_release_gpu(w.prog + b, w.base + (unsigned)s + 1u);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
 }
@@ -667,9 +723,13 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
 
 // ---- batched TMA kernel ---------------------------------------------------
 // The single-lattice pipeline over the concatenated row tiles of all cases:
-// the producer finds the case of each tile, stages its rows and passes
-// (case, row, tile) to the compute warps through a shared-memory slot of the
-// stage, published by the same mbarrier that counts the copied bytes.
+// the producer finds the case of each tile, stages its rows and the case's
+// step parameters (one more bulk copy, into the stage's parameter slot) and
+// passes (case, row, tile) to the compute warps through a shared-memory slot
+// of the stage, all published by the same mbarrier that counts the copied
+// bytes.  The compute warps read the parameters from shared memory, not from
+// the descriptor array in global memory, and release the stage only when
+// they no longer need them.
 template <class S, int NCW, int CPT, int STAGES, int MRT>
 __global__ void __launch_bounds__((NCW + 1) * 32)
     step_tma_batch(const CaseDesc *__restrict__ cases, int ncases, long long nitems, int parity) {
@@ -683,10 +743,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
   S *tiles = reinterpret_cast<S *>(smem);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
   __shared__ int4 info[STAGES];
+  __shared__ StepParams sp[STAGES];
   __shared__ double red[2][NCW];
   __shared__ int s_last;
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
+  static_assert(sizeof(StepParams) % 16 == 0, "bulk copy of the step parameters");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) {
@@ -728,8 +790,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         }
         info[st] = make_int4(c, y, s, 0);
         const uint32_t fb = smem_addr(&bars[st]);
-        mbar_arrive_expect_tx(fb, total);
+        mbar_arrive_expect_tx(fb, total + (uint32_t)sizeof(StepParams));
         if (tl == p.fault_tile) continue;  // failure-path test: announced, never copied
+        bulk_g2s(smem_addr(&sp[st]), &cases[c].p, (uint32_t)sizeof(StepParams), fb);
         S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
         for (int k = 0; k < 9; ++k)
@@ -778,14 +841,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
       y = tl / cases[c].p.nseg;
       s = tl - y * cases[c].p.nseg;
     }
-    const StepParams &p = cases[c].p;
     const S *__restrict__ A = (const S *)cases[c].buf[parity];
     S *__restrict__ B = (S *)cases[c].buf[parity ^ 1];
-    const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
     const int x0 = s * W;
-    double fx = 0.0, fy = 0.0;
-    bool bad = false;
     if (ok) {
+      const StepParams &p = sp[st];
+      const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
+      double fx = 0.0, fy = 0.0;
+      bool bad = false;
       const S *tile = tiles + (size_t)st * 9 * SEG + (H - x0);
       auto fetch = [&](int k, int sx, int) -> C { return Store<S>::ld(tile[k * SEG + sx]); };
 #pragma unroll
@@ -806,11 +869,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
             update_node<MRT, S>(A, B, p, x, y, cf, fetch, fx, fy, bad);
         }
       }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
+      if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));
+      if (lane == 0) mbar_arrive(smem_addr(&bars[STAGES + st]));  // the stage, parameters included, is free
+    } else {
+      const StepParams &p = cases[c].p;
+      if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, 0.0, 0.0, ctid, red, s_last, [] { named_bar(1, NC); });
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_UNSTABLE);
-    if (is_force_item(p, y, s)) post_force<NCW>(p, y, s, fx, fy, ctid, red, s_last, [] { named_bar(1, NC); });
   }
 }
 
@@ -1258,15 +1324,15 @@ struct Launch {
     }
     if (mode == 2) {  // resident CTAs per SM into *occ
       int n = 0, m = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k0, (NCW + 1) * 32, smem) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k1, (NCW + 1) * 32, smem) != cudaSuccess)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k0, (NCW + 2) * 32, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k1, (NCW + 2) * 32, smem) != cudaSuccess)
         return cudaErrorInvalidConfiguration;
       *occ = n < m ? n : m;
       return cudaSuccess;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((NCW + 1) * 32);
+    cfg.blockDim = dim3((NCW + 2) * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

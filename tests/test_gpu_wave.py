@@ -1,9 +1,9 @@
 """The multi-step kernel (LBM_KERNEL_TMA_WAVE) against the one-step TMA
 kernel: the same bits in populations and force histories, whatever the
-storage form, boundary rule, collision model, band layout (bands of one
-tile, of less than a row, of many rows) or split of the steps into
-launches; one run against the FP64 oracle; its failure path and its argument
-checks."""
+storage form, boundary rule, collision model, tiling (fewer tiles than CTAs,
+a few more, many more; rows of one tile or several) or split of the steps
+into launches; one run against the FP64 oracle; its failure path and its
+argument checks."""
 import numpy as np
 import pytest
 
@@ -48,7 +48,8 @@ def same(a, b):
 @pytest.mark.parametrize("bc", BCS, ids=["freeslip", "periodic", "zouhe", "movingwall"])
 def test_wave_bitwise_equals_one_step_kernel(storage, bc):
     # 401 x 77: 512-node (float, double) or 768-node (16-bit) tiles, one per
-    # row: 77 CTAs of one tile each; 150 steps = launches of 64, 64, 22
+    # row: 77 CTAs of one tile each, so a tile of step s waits for tiles of
+    # step s - 1 on other CTAs; 150 steps = launches of 64, 64, 22
     wl = W.random_case(401, 77, seed=3 + bc, bc=bc, D=12)
     mrt = (bc + storage) % 2 == 1
     ctas = 2 if lbm.ELEM_BYTES[storage] == 2 else 1
@@ -59,11 +60,11 @@ def test_wave_bitwise_equals_one_step_kernel(storage, bc):
 
 
 @pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_FREESLIP], ids=["periodic", "freeslip"])
-def test_wave_bands_shorter_than_a_row(bc):
-    # 3000 x 50 with 768-node tiles: 4 tiles a row, 200 tiles on 152 CTAs,
-    # so a band holds one or two tiles and a row's neighbours span several
-    # CTAs (with the periodic wrap between the first and the last ones);
-    # launches of 1, 63, 64, 65 (= 64 + 1) and 7 steps
+def test_wave_uneven_tiling(bc):
+    # 3000 x 50 with 768-node tiles: 4 tiles a row, 200 tiles on 152 CTAs, so
+    # some CTAs run two tiles a step and others one, and a row's tiles sit on
+    # several CTAs (periodic: rows 0 and 49 depend on each other); launches of
+    # 1, 63, 64, 65 (= 64 + 1) and 7 steps
     wl = W.random_case(3000, 50, seed=11, bc=bc, D=14)
     chunks = [1, 63, 64, 65, 7]
     ref = run(wl, chunks, lbm.LBM_KERNEL_TMA)
@@ -73,8 +74,8 @@ def test_wave_bands_shorter_than_a_row(bc):
 
 
 @pytest.mark.parametrize("shape", [(8, 2, 4), (12, 2, 4), (10, 2, 4), (13, 2, 3)])
-def test_wave_bands_of_many_rows_every_shape(shape):
-    # 1601 x 900 (ragged last tile): several rows per band on 152 CTAs
+def test_wave_many_tiles_per_cta_every_shape(shape):
+    # 1601 x 900 (ragged last tile): thousands of tiles a step on 152 CTAs
     wl = W.random_case(1601, 900, seed=17, bc=W.BC_ZOUHE, D=40)
     ncw, cpt, st = shape
     a = lbm.lattice_for(wl, kernel=lbm.LBM_KERNEL_TMA)
