@@ -422,15 +422,15 @@ __global__ void __launch_bounds__((NCW + 1) * 32) step_tma(const S *__restrict__
 // it pulls, and have read the rows it will overwrite).  A CTA can therefore
 // start the next step's first rows while other CTAs finish the last rows of
 // the step before: no pipeline fill and no tail per step.
-// CTA = NCW compute warps, the producer warp, and a publisher warp that
-// waits for each tile's "done" mbarrier (all compute warps finished it), adds
-// the tile to its row's counter (a batch of tiles per GPU-scope fence) and
-// then frees the stage on a third mbarrier, the one the producer waits on
-// before it reuses the stage: producer, compute warps and publisher so stay
-// within one phase of each other on every stage, which the parity waits
-// need.  The publisher depends on nothing but this CTA's compute warps, so a
-// producer waiting on a counter never holds back a completion another CTA
-// waits for.  The producer checks the rows of the next WAVE_AHEAD tiles with
+// CTA = NCW compute warps, the producer warp, and a publisher warp.  The
+// producer sees a tile finished on its stage's "empty" mbarrier (all compute
+// warps done with it) -- when it reuses the stage, and by polling the stages
+// in flight while it waits on a counter -- and advances a shared-memory count
+// of finished tiles (release, CTA scope).  The publisher follows that count
+// and adds each finished tile to its row's counter, a batch of tiles per
+// GPU-scope fence, off the producer's path.  A producer waiting on a counter
+// keeps reporting its finished tiles, so no CTA waits on a completion that
+// another wait holds back.  The producer checks the rows of the next WAVE_AHEAD tiles with
 // one round of independent loads.
 // Per node the arithmetic is that of step_tma, so the results are the same
 // bits; the node's own previous values are read through L2 (they were
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
   extern __shared__ __align__(128) unsigned char smem[];
   S *tiles = reinterpret_cast<S *>(smem);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
-  __shared__ uint64_t freed[STAGES];  // publisher -> producer: stage free again
+  __shared__ unsigned s_finished;  // producer -> publisher: tiles [0, s_finished) finished
   __shared__ double red[2][NCW];
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
@@ -475,8 +475,8 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
     for (int q = 0; q < STAGES; ++q) {
       mbar_init(smem_addr(&bars[q]), 1);
       mbar_init(smem_addr(&bars[STAGES + q]), NCW);
-      mbar_init(smem_addr(&freed[q]), 1);
     }
+    s_finished = 0;
     *s_abort = 0;
     mbar_fence_init();
   }
@@ -484,28 +484,28 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
 
   if (warp == NCW + 1) {  // ---------------- publisher
     if (lane == 0) {
-      const long long total = (long long)per_step * w.steps;
-      long long q = 0;
-      int k = 0;  // in-step index of tile q
-      while (q < total) {
-        if (!mbar_wait_bounded(smem_addr(&bars[STAGES + (int)(q % STAGES)]), (unsigned)((q / STAGES) & 1), s_abort,
-                               p.wait_ns)) {
-          if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
-          *s_abort = 1;
-          break;
+      const unsigned total = (unsigned)per_step * (unsigned)w.steps;
+      unsigned q = 0;
+      int kk = 0;  // in-step index of tile q
+      unsigned long long t0 = global_ns();
+      const unsigned long long lim = wait_limit(p.wait_ns);
+      while (q < total && !*s_abort) {
+        const unsigned c = ld_acquire_cta_shared(&s_finished);
+        if (c == q) {
+          if (global_ns() - t0 > lim) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            *s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
+          continue;
         }
-        int n = 1;  // and every later tile already done, without waiting
-        while (n < STAGES && q + n < total &&
-               mbar_test_wait(smem_addr(&bars[STAGES + (int)((q + n) % STAGES)]), (unsigned)(((q + n) / STAGES) & 1)))
-          ++n;
         fence_acq_rel_gpu();
-        for (int i = 0; i < n; ++i) {
-          const int y = ((int)blockIdx.x + k * G) / p.nseg;
-          red_relaxed_gpu_add(w.rows_done + y, 1u);
-          if (++k == per_step) k = 0;
+        for (; q < c; ++q) {
+          red_relaxed_gpu_add(w.rows_done + ((int)blockIdx.x + kk * G) / p.nseg, 1u);
+          if (++kk == per_step) kk = 0;
         }
-        for (int i = 0; i < n; ++i) mbar_arrive(smem_addr(&freed[(int)((q + i) % STAGES)]));
-        q += n;
+        t0 = global_ns();
       }
     }
     return;
@@ -513,7 +513,16 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
 
   if (warp == NCW) {  // ---------------- producer
     if (lane == 0) {
-      int j = 0;  // tiles issued (all steps of this launch)
+      int j = 0;     // tiles issued (all steps of this launch)
+      int fin = 0;   // tiles [0, fin) finished and reported
+      // report the finished prefix of the tiles in flight (non-blocking);
+      // a stage is reused only after its tile finished, so each parity test
+      // refers to the tile in flight on it
+      auto collect = [&]() {
+        const int f0 = fin;
+        while (fin < j && mbar_test_wait(smem_addr(&bars[STAGES + fin % STAGES]), (fin / STAGES) & 1)) ++fin;
+        if (fin != f0) st_release_cta_shared(&s_finished, (unsigned)fin);
+      };
       bool stop = false;
       for (int s = 0; s < w.steps && !stop; ++s) {
         const S *A = (s & 1) ? buf1 : buf0;
@@ -522,11 +531,15 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
         int k = 0;
         for (int t = blockIdx.x; t < nitems; t += G, ++j, ++k) {
           const int st = j % STAGES;
-          if (j >= STAGES && !mbar_wait_bounded(smem_addr(&freed[st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
-            if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
-            *s_abort = 1;
-            stop = true;
-            break;
+          if (j >= STAGES) {
+            if (fin <= j - STAGES &&
+                !mbar_wait_bounded(smem_addr(&bars[STAGES + st]), ((j / STAGES) - 1) & 1, s_abort, p.wait_ns)) {
+              if (!*s_abort) atomicOr(p.err, ERR_TIMEOUT);
+              *s_abort = 1;
+              stop = true;
+              break;
+            }
+            collect();
           }
           if (*s_abort) {
             stop = true;
@@ -553,6 +566,7 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
                 ver = k + m;
                 break;
               }
+              collect();
               if ((*(volatile const unsigned *)p.err & ERR_TIMEOUT) || global_ns() - t0 > lim) break;
             }
             if (k >= ver) {
@@ -588,12 +602,14 @@ __global__ void __launch_bounds__((NCW + 2) * 32)
                        bytes, fb);
         }
       }
-      // Do not leave while a copy into this CTA's shared memory is in flight.
+      // Report the last tiles, and do not leave while a copy into this CTA's
+      // shared memory is in flight (bounded waits).
+      const unsigned long long t0 = global_ns(), lim = wait_limit(p.wait_ns);
+      while (fin < j && !*s_abort && global_ns() - t0 <= lim) collect();
       for (int q = max(0, j - STAGES); q < j; ++q) {
         const uint32_t fb = smem_addr(&bars[q % STAGES]);
-        const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(fb, (q / STAGES) & 1)) {
-          if (global_ns() - t0 > wait_limit(p.wait_ns)) {
+          if (global_ns() - t0 > lim) {
             atomicOr(p.err, ERR_TIMEOUT);
             break;
           }
@@ -724,7 +740,8 @@ __global__ void __launch_bounds__(NT) step_direct_batch(const CaseDesc *__restri
 // ---- batched TMA kernel ---------------------------------------------------
 // The single-lattice pipeline over the concatenated row tiles of all cases:
 // the producer finds the case of each tile, stages its rows and the case's
-// step parameters (one more bulk copy, into the stage's parameter slot) and
+// descriptor (step parameters and buffers: one more bulk copy, into the
+// stage's descriptor slot) and
 // passes (case, row, tile) to the compute warps through a shared-memory slot
 // of the stage, all published by the same mbarrier that counts the copied
 // bytes.  The compute warps read the parameters from shared memory, not from
@@ -743,12 +760,12 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
   S *tiles = reinterpret_cast<S *>(smem);
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)STAGES * 9 * SEG * sizeof(S));
   __shared__ int4 info[STAGES];
-  __shared__ StepParams sp[STAGES];
+  __shared__ CaseDesc sp[STAGES];
   __shared__ double red[2][NCW];
   __shared__ int s_last;
   __shared__ int s_abort_store;
   volatile int *s_abort = &s_abort_store;
-  static_assert(sizeof(StepParams) % 16 == 0, "bulk copy of the step parameters");
+  static_assert(sizeof(CaseDesc) % 16 == 0, "bulk copy of a case descriptor");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) {
@@ -790,9 +807,9 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
         }
         info[st] = make_int4(c, y, s, 0);
         const uint32_t fb = smem_addr(&bars[st]);
-        mbar_arrive_expect_tx(fb, total + (uint32_t)sizeof(StepParams));
+        mbar_arrive_expect_tx(fb, total + (uint32_t)sizeof(CaseDesc));
         if (tl == p.fault_tile) continue;  // failure-path test: announced, never copied
-        bulk_g2s(smem_addr(&sp[st]), &cases[c].p, (uint32_t)sizeof(StepParams), fb);
+        bulk_g2s(smem_addr(&sp[st]), &cases[c], (uint32_t)sizeof(CaseDesc), fb);
         S *dst = tiles + (size_t)st * 9 * SEG + (xs - (x0 - H));
 #pragma unroll
         for (int k = 0; k < 9; ++k)
@@ -841,11 +858,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32)
       y = tl / cases[c].p.nseg;
       s = tl - y * cases[c].p.nseg;
     }
-    const S *__restrict__ A = (const S *)cases[c].buf[parity];
-    S *__restrict__ B = (S *)cases[c].buf[parity ^ 1];
     const int x0 = s * W;
     if (ok) {
-      const StepParams &p = sp[st];
+      const StepParams &p = sp[st].p;
+      const S *__restrict__ A = (const S *)sp[st].buf[parity];
+      S *__restrict__ B = (S *)sp[st].buf[parity ^ 1];
       const Coef<Lane<S>> cf = make_coef<Lane<S>>(p);
       double fx = 0.0, fy = 0.0;
       bool bad = false;
