@@ -45,9 +45,9 @@ UNIT = "GLUPS"
 # Taken on the 8000 x 4000 lattice of the same geometry (32M nodes, 2.3 GB of
 # FP32 populations, far above L2) in the 768-node-tile shape the 16000 x 8000
 # lattice uses; traffic per node does not depend on the lattice size.
-NCU_TRAFFIC = {"digest": "97b83b946e2178f9",
-               "bytes_per_node": {"f32": (1154373120 + 1102585088) / 32e6, "bf16sr": (594746368 + 532244736) / 32e6,
-                                  "f16sr": (594688768 + 531981824) / 32e6}}
+NCU_TRAFFIC = {"digest": "749fa125f3d3d2f5",
+               "bytes_per_node": {"f32": (1154348288 + 1102509824) / 32e6, "bf16sr": (593798144 + 532119808) / 32e6,
+                                  "f16sr": (594534656 + 531918080) / 32e6}}
 
 # The paper's own Re = 100 results (Table 2, "present work": MRT, D = 20,
 # U = 0.02, 800 x 400), quoted as context; the paper states no hardware.
