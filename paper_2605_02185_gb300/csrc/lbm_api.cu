@@ -68,6 +68,28 @@ int find_shape(int kernel, int ncw, int cpt, int stages) {
   return -1;
 }
 
+// The kernel, shape and CTAs per SM a context asks for: AUTO takes the
+// storage type's default kernel; an explicit shape (ncw, cpt, stages) is
+// looked up in the kernel's list (-1 if absent), else the default shape of
+// the lattice size; ctas_per_sm <= 0 takes the default of that shape for
+// the TMA kernels and 1 for the others.  Returns the kernel or -1.
+int choose_kernel(int storage, int nx, int ny, bool interp, int kernel, int ncw, int cpt, int stages, int ctas_per_sm,
+                  int *shape, int *ctas) {
+  if (kernel == LBM_KERNEL_AUTO) kernel = default_kernel(storage);
+  const DefaultShape d = default_shape(storage, (long long)nx * ny, interp || kernel == LBM_KERNEL_TMA_WAVE);
+  *ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
+  if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
+    *shape = find_shape(kernel, ncw, cpt, stages);
+    if (*shape < 0) return -1;
+  } else if (kernel == LBM_KERNEL_TMA_BULK) {
+    *shape = 0;
+  } else {
+    *shape = d.shape;
+    if (ctas_per_sm <= 0 && kernel != LBM_KERNEL_DIRECT) *ctas = d.ctas;
+  }
+  return kernel;
+}
+
 // Fill the step parameters for the chosen kernel shape (tile width, force
 // slots) and capture the multi-step graph.
 int configure_kernel(lbm_ctx *c, int kernel, int shape, int ctas_per_sm) {
@@ -344,17 +366,10 @@ int lbm_create_ex(const lbm_opts *o, const uint8_t *mask, lbm_ctx **out) {
   p.wait_ns = 1000000000ull;  // every bounded device wait gives up after 1 s
   p.fault_tile = -1;
 
-  int shape = default_shape(o->storage, o->nx);
-  int kernel = o->kernel;
-  int ctas = o->ctas_per_sm > 0 ? o->ctas_per_sm : 1;
-  if (kernel == LBM_KERNEL_TMA_BULK) shape = 0;
-  if (o->consumer_warps || o->cells_per_thread || o->stages) {
-    shape = find_shape(kernel, o->consumer_warps, o->cells_per_thread, o->stages);
-    if (shape < 0 && kernel != LBM_KERNEL_DIRECT) return fail(LBM_ERR_ARG);
-  } else if (kernel == LBM_KERNEL_AUTO) {
-    kernel = default_kernel(o->storage);
-    if (o->ctas_per_sm <= 0) ctas = default_ctas(o->storage);
-  }
+  int shape = -1, ctas = 1;
+  const int kernel = choose_kernel(o->storage, o->nx, o->ny, !c->geo.qmap.empty(), o->kernel, o->consumer_warps,
+                                   o->cells_per_thread, o->stages, o->ctas_per_sm, &shape, &ctas);
+  if (kernel < 0) return fail(LBM_ERR_ARG);
   rc = configure_kernel(c, kernel, std::max(shape, 0), ctas);
   if (rc) return fail(rc);
   rc = capture_graph(c);
@@ -580,16 +595,11 @@ int lbm_set_kernel(lbm_ctx *c, int kernel, int ncw, int cpt, int stages, int cta
   if (!c || kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA_WAVE) return LBM_ERR_ARG;
   CK(cudaSetDevice(c->dev));
   CK(cudaStreamSynchronize(c->stream));
-  int shape = kernel == LBM_KERNEL_TMA_BULK ? 0 : default_shape(c->o.storage, c->nx);
-  int ctas = ctas_per_sm > 0 ? ctas_per_sm : 1;
-  if (kernel != LBM_KERNEL_DIRECT && (ncw || cpt || stages)) {
-    shape = find_shape(kernel, ncw, cpt, stages);
-    if (shape < 0) return LBM_ERR_ARG;
-  } else if (kernel == LBM_KERNEL_AUTO) {
-    kernel = default_kernel(c->o.storage);
-    if (ctas_per_sm <= 0) ctas = default_ctas(c->o.storage);
-  }
-  const int rc = configure_kernel(c, kernel, shape, ctas);
+  int shape = -1, ctas = 1;
+  kernel = choose_kernel(c->o.storage, c->nx, c->ny, c->qmap != nullptr, kernel, ncw, cpt, stages, ctas_per_sm, &shape,
+                         &ctas);
+  if (kernel < 0) return LBM_ERR_ARG;
+  const int rc = configure_kernel(c, kernel, std::max(shape, 0), ctas);
   if (rc) return rc;
   return capture_graph(c);
 }

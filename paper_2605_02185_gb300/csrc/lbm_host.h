@@ -163,33 +163,33 @@ inline int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-// Defaults from the shape sweep on the 16000 x 8000 lattice: float storage
-// (12 compute warps, 2 nodes/thread, 4 stages, 1 CTA/SM) reaches ~95% of the
-// measured copy bandwidth; 16-bit storage the same shape at 2 CTAs/SM;
-// double storage is FP64-ALU bound and runs best on the direct kernel.
-// Default TMA shape.  Float storage: 12 compute warps x 2 nodes (768-node
-// row tiles, the fastest on wide lattices) unless the lattice width wastes
-// more than 2 % of a last, partial tile on it; then the 640- or 512-node tile
-// that wastes least (3200 x 1600: 72.9 against 67.7 GLUPS with 640).
-inline int default_shape(int storage, int nx) {
-  if (storage == LBM_F64) return 6;
-  if (storage != LBM_F32 || nx <= 0) return 12;
-  const int ids[3] = {12, 15, 6};  // (12, 2, 4), (10, 2, 4), (8, 2, 4)
-  const int widths[3] = {768, 640, 512};
-  int best = 12;
-  double best_waste = 2.0;
-  for (int i = 0; i < 3; ++i) {
-    const int tiles = (nx + widths[i] - 1) / widths[i];
-    const double waste = (double)(tiles * widths[i] - nx) / nx;
-    if (i == 0 && waste <= 0.02) return 12;
-    if (waste < best_waste - 1e-12) {
-      best_waste = waste;
-      best = ids[i];
-    }
-  }
-  return best;
+// Default TMA shape (an index into GBLBM_TMA_SHAPES) and CTAs per SM of a
+// single lattice, from a sweep of every shape at 1 and 2 CTAs/SM on FP32
+// cylinder lattices (CUDA events, BGK):
+//   >= 16M nodes (16000 x 8000, 8000 x 4000): 12 compute warps x 2 nodes,
+//     4 stages (768-node tiles), 1 CTA/SM -- 90.2 and 89.3 GLUPS (the 512-node
+//     tile that wastes least on an 8000-node row ran at 59.3);
+//   3M .. 16M nodes (3200 x 1600): 16 warps x 1 node, 4 stages (512-node
+//     tiles), 2 CTAs/SM -- 77.6 against 73.3 for 640-node tiles at 1 CTA/SM;
+//   < 3M nodes (1600 x 800): 10 warps x 2 nodes, 4 stages (640-node tiles),
+//     2 CTAs/SM -- 58.7 against 50.6 at 1 CTA/SM.
+// 16-bit storage: 12 x 2 x 4 at 2 CTAs/SM (95 % of the 16-bit roofline on
+// 16000 x 8000); double storage: 8 x 2 x 4 at 1 CTA/SM (FP64-ALU bound; it
+// runs on the direct kernel by default).  The TMA kernel with interpolated
+// bounce-back and the multi-step kernel are built for fewer shapes
+// (few_shapes): there float storage takes 12 x 2 x 4 from 16M nodes up and
+// 10 x 2 x 4 below, at 1 CTA/SM.
+struct DefaultShape {
+  int shape, ctas;
+};
+inline DefaultShape default_shape(int storage, long long nodes, bool few_shapes) {
+  if (storage == LBM_F64) return {6, 1};
+  if (storage != LBM_F32) return {12, 2};
+  if (nodes >= (16ll << 20)) return {12, 1};
+  if (few_shapes) return {15, 1};
+  if (nodes >= (3ll << 20)) return {11, 2};
+  return {15, 2};
 }
-inline int default_ctas(int storage) { return elem_size(storage) == 2 ? 2 : 1; }
 // Batches of many small lattices: shape 19 (13 compute warps, 2 cells per
 // thread, 3 stages: 832-node row tiles, which fit rows of 800-2400 nodes with
 // little waste) at 2 CTAs per SM, the autotuner's pick for 64 cases of
