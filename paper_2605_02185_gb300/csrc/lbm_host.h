@@ -173,8 +173,9 @@ inline int cuda_fail(cudaError_t e) {
 //     tiles), 2 CTAs/SM -- 77.6 against 73.3 for 640-node tiles at 1 CTA/SM;
 //   < 3M nodes (1600 x 800): 10 warps x 2 nodes, 4 stages (640-node tiles),
 //     2 CTAs/SM -- 58.7 against 50.6 at 1 CTA/SM.
-// 16-bit storage: 12 x 2 x 4 at 2 CTAs/SM (95 % of the 16-bit roofline on
-// 16000 x 8000); double storage: 8 x 2 x 4 at 1 CTA/SM (FP64-ALU bound; it
+// 16-bit storage: 12 x 2 x 4 at 2 CTAs/SM (the fastest shape for all four
+// 16-bit forms on 16000 x 8000, 0.89 of the copy bandwidth with rounding to
+// nearest); double storage: 8 x 2 x 4 at 1 CTA/SM (FP64-ALU bound; it
 // runs on the direct kernel by default).  The TMA kernel with interpolated
 // bounce-back and the multi-step kernel are built for fewer shapes
 // (few_shapes): there float storage takes 12 x 2 x 4 from 16M nodes up and
