@@ -194,7 +194,8 @@ inline DefaultShape default_shape(int storage, long long nodes, bool few_shapes)
 // Batches of many small lattices: shape 19 (13 compute warps, 2 cells per
 // thread, 3 stages: 832-node row tiles, which fit rows of 800-2400 nodes with
 // little waste) at 2 CTAs per SM, the autotuner's pick for 64 cases of
-// 800-2400 nodes wide (62 GLUPS, 1.76x the same cases one after another).
+// 800-2400 nodes wide (67-68 GLUPS with MRT, 1.48x the same cases run one after
+// another as single lattices in their default shapes).
 inline int default_batch_shape(int storage) { return storage == LBM_F64 ? 6 : 19; }
 inline int default_batch_ctas(int storage) { return storage == LBM_F64 ? 1 : 2; }
 inline int default_kernel(int storage) { return storage == LBM_F64 ? LBM_KERNEL_DIRECT : LBM_KERNEL_TMA; }
