@@ -91,7 +91,11 @@ extern "C" {
                                  half-way bounce-back only (interpolated
                                  bounce-back runs on the kernels named under
                                  lbm_opts.bounce).  No CUDA graph is captured
-                                 for it. */
+                                 for it.  An option, not the default: on the
+                                 1.3M-32M-node lattices measured it is 7-27 %
+                                 slower than LBM_KERNEL_TMA (its per-tile
+                                 synchronisation costs more than the launch
+                                 boundaries it removes). */
 
 typedef struct lbm_ctx lbm_ctx;
 
