@@ -371,6 +371,31 @@ def evaluate_case(pred: nn.WarmStartNet, Re: float, cfg: Config, device, seed: i
     return out
 
 
+def summarize(rows):
+    """Summary of evaluated cases (dicts as evaluate_case returns them).
+
+    Time with the warm start as the first try, over every judged case (one
+    whose cold start became periodic): a rejected or never-periodic warm run
+    costs its own time (up to the step limit) and then the cold run's, so the
+    gain of a case is cold time / (warm time if accepted, else warm time +
+    cold time).  Adds cost_s and gain to each judged row."""
+    acc = [r for r in rows if r["accepted"]]
+    judged = [r for r in rows if r["cold_periodic"]]
+    for r in judged:
+        warm_t = r["warm"]["wall_s"] if r["warm"]["wall_s"] is not None else r["warm"].get("limit_s", 0.0)
+        r["cost_s"] = warm_t if r["accepted"] else warm_t + r["cold"]["wall_s"]
+        r["gain"] = r["cold"]["wall_s"] / r["cost_s"]
+    summary = {
+        "cases": len(rows), "cold_periodic": len(judged), "accepted": len(acc),
+        "median_gain_all_judged": float(np.median([r["gain"] for r in judged])) if judged else None,
+        "total_time_speedup": (sum(r["cold"]["wall_s"] for r in judged) / sum(r["cost_s"] for r in judged))
+        if judged else None,
+        "median_step_speedup_accepted": float(np.median([r["step_speedup"] for r in acc])) if acc else None,
+        "median_time_speedup_accepted": float(np.median([r["time_speedup"] for r in acc])) if acc else None,
+    }
+    return summary
+
+
 def evaluate(net, cfg: Config, n_eval: int = 16, device=None, log=print):
     import torch
     device = device or torch.device("cuda")
@@ -384,22 +409,5 @@ def evaluate(net, cfg: Config, n_eval: int = 16, device=None, log=print):
             f"warm {r['warm']['steps']} steps {fmt(r['warm']['wall_s'])}, accepted {r['accepted']}, "
             f"drift {r.get('drift')}")
         rows.append(r)
-    acc = [r for r in rows if r["accepted"]]
-    judged = [r for r in rows if r["cold_periodic"]]
-    # Time with the warm start as the first try, over every judged case: a
-    # rejected or never-periodic warm run costs its own time (up to the step
-    # limit) and then the cold run's, so the gain of a case is
-    # cold time / (warm time if accepted, else warm time + cold time).
-    for r in judged:
-        warm_t = r["warm"]["wall_s"] if r["warm"]["wall_s"] is not None else r["warm"].get("limit_s", 0.0)
-        r["cost_s"] = warm_t if r["accepted"] else warm_t + r["cold"]["wall_s"]
-        r["gain"] = r["cold"]["wall_s"] / r["cost_s"]
-    summary = {
-        "cases": len(rows), "cold_periodic": len(judged), "accepted": len(acc),
-        "median_gain_all_judged": float(np.median([r["gain"] for r in judged])) if judged else None,
-        "total_time_speedup": (sum(r["cold"]["wall_s"] for r in judged) / sum(r["cost_s"] for r in judged))
-        if judged else None,
-        "median_step_speedup_accepted": float(np.median([r["step_speedup"] for r in acc])) if acc else None,
-        "median_time_speedup_accepted": float(np.median([r["time_speedup"] for r in acc])) if acc else None,
-    }
+    summary = summarize(rows)
     return rows, summary
