@@ -144,7 +144,8 @@ typedef struct lbm_opts {
 #define LBM_BOUNCE_HALFWAY 0
 #define LBM_BOUNCE_INTERPOLATED 1
 
-/* Defaults: F32 storage, BGK, MRT rates 1.1, auto kernel, free-slip,
+/* Defaults: F32 storage, BGK, MRT rates 1.1, auto kernel with the tuned
+ * shape and CTAs per SM of the lattice size (ctas_per_sm 0), free-slip,
  * capacity 1 << 20. */
 int lbm_opts_default(lbm_opts *opts);
 
@@ -249,6 +250,16 @@ int lbm_set_kernel(lbm_ctx *ctx, int kernel, int consumer_warps, int cells_per_t
 /* The kernel shape in use: kernel, consumer warps, cells/thread, stages,
  * CTAs per SM, grid size (CTAs) -- 6 ints. */
 int lbm_get_kernel(lbm_ctx *ctx, int *out6);
+
+/* Host only (no GPU call): the kernel, consumer warps, cells/thread, stages
+ * and CTAs per SM (5 ints into out5) that lbm_create_ex picks for *opts
+ * before it checks them against the device -- LBM_KERNEL_AUTO resolved, the
+ * default shape of the lattice size where none is given, ctas_per_sm 0
+ * resolved.  A shape given in opts that the kernel is not built for is
+ * LBM_ERR_ARG, as are options lbm_create_ex would refuse.  (Interpolated
+ * bounce-back on a storage type or shape without its TMA kernel runs on the
+ * direct kernel; that choice is made on creation, not here.) */
+int lbm_default_kernel(const lbm_opts *opts, int *out5);
 
 /* The shapes the TMA kernel is built for: up to cap triples (compute warps,
  * cells per thread, stages) into out; *count receives how many exist. */

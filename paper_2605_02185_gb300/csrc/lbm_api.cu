@@ -246,7 +246,7 @@ int lbm_opts_default(lbm_opts *o) {
   o->storage = LBM_F32;
   o->history_capacity = 1ll << 20;
   o->kernel = LBM_KERNEL_AUTO;
-  o->ctas_per_sm = 1;
+  o->ctas_per_sm = 0;  // the tuned default of the chosen shape
   o->collision = LBM_COLLIDE_BGK;
   o->s_e = o->s_eps = o->s_q = 1.1;
   return LBM_OK;
@@ -615,6 +615,29 @@ int lbm_set_fault_injection(lbm_ctx *c, int64_t tile, double wait_seconds) {
   c->p.wait_ns = wait_seconds > 0 ? (unsigned long long)(wait_seconds * 1e9) : 1000000000ull;
   if (c->p.wait_ns == 0) c->p.wait_ns = 1;
   return capture_graph(c);
+}
+
+int lbm_default_kernel(const lbm_opts *o, int *out5) {
+  const int rc = check_opts(o);
+  if (rc) return rc;
+  if (!out5) return LBM_ERR_ARG;
+  int shape = -1, ctas = 1;
+  const int kernel = choose_kernel(o->storage, o->nx, o->ny, o->bounce == LBM_BOUNCE_INTERPOLATED, o->kernel,
+                                   o->consumer_warps, o->cells_per_thread, o->stages, o->ctas_per_sm, &shape, &ctas);
+  if (kernel < 0) return LBM_ERR_ARG;
+  if (kernel == LBM_KERNEL_TMA_WAVE) {  // built for fewer shapes
+    bool built = false;
+    for (int i = 0; i < kNumWaveShapes; ++i) built = built || kWaveShapes[i].id == shape;
+    if (!built) return LBM_ERR_ARG;
+  }
+  const bool tma = kernel != LBM_KERNEL_DIRECT;
+  const TmaShape &sh = kernel == LBM_KERNEL_TMA_BULK ? kTmaBulkShapes[shape] : kTmaShapes[std::max(shape, 0)];
+  out5[0] = kernel;
+  out5[1] = tma ? sh.ncw : kDirectThreads / 32;
+  out5[2] = tma ? sh.cpt : 1;
+  out5[3] = tma ? sh.stages : 0;
+  out5[4] = tma ? ctas : 0;
+  return LBM_OK;
 }
 
 int lbm_get_kernel(lbm_ctx *c, int *out6) {

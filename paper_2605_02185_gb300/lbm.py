@@ -102,6 +102,7 @@ def load_library(path: str | None = None):
         "lbm_get_window": (i, [vp, i, i, i, i, vp]),
         "lbm_set_kernel": (i, [vp, i, i, i, i, i]),
         "lbm_get_kernel": (i, [vp, vp]),
+        "lbm_default_kernel": (i, [ctypes.POINTER(lbm_opts), vp]),
         "lbm_kernel_shapes": (i, [vp, i, ctypes.POINTER(i)]),
         "lbm_kernel_shapes_for": (i, [i, vp, i, ctypes.POINTER(i)]),
         "lbm_get_stream": (i, [vp, ctypes.POINTER(vp)]),
@@ -342,6 +343,13 @@ def lbm_get_kernel(h) -> dict:
     out = np.zeros(6, np.int32)
     _check(load_library().lbm_get_kernel(h, _p(out)), "lbm_get_kernel")
     keys = ("kernel", "consumer_warps", "cells_per_thread", "stages", "ctas_per_sm", "grid")
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+def lbm_default_kernel(opts: lbm_opts) -> dict:
+    out = np.zeros(5, np.int32)
+    _check(load_library().lbm_default_kernel(ctypes.byref(opts), _p(out)), "lbm_default_kernel")
+    keys = ("kernel", "consumer_warps", "cells_per_thread", "stages", "ctas_per_sm")
     return dict(zip(keys, (int(v) for v in out)))
 
 

@@ -52,6 +52,7 @@ def test_host_only_entry_points(lib):
     assert lbm.lbm_error_string(lbm.LBM_ERR_ARG) == "invalid argument or geometry"
     o = lbm.lbm_opts_default()
     assert o.storage == lbm.LBM_F32 and o.history_capacity == 1 << 20
+    assert o.kernel == lbm.LBM_KERNEL_AUTO and o.ctas_per_sm == 0
     o.nx, o.ny, o.tau, o.U = 400, 200, 0.53, 0.1
     mask = np.zeros((200, 400), np.uint8)
     mask[95:106, 95:106] = 1
@@ -60,6 +61,28 @@ def test_host_only_entry_points(lib):
     assert b >= 2 * 9 * 200 * 448 * 4
     o.storage = lbm.LBM_F16_OFS
     assert lbm.lbm_workspace_bytes(o, mask) < b
+    # default kernel and shape by lattice size (host only)
+    def default(nx, ny, **kw):
+        q = lbm.lbm_opts_default()
+        q.nx, q.ny, q.tau, q.U = nx, ny, 0.6, 0.05
+        for k, v in kw.items():
+            setattr(q, k, v)
+        d = lbm.lbm_default_kernel(q)
+        return d["kernel"], (d["consumer_warps"], d["cells_per_thread"], d["stages"]), d["ctas_per_sm"]
+    T = lbm.LBM_KERNEL_TMA
+    assert default(16000, 8000) == (T, (12, 2, 4), 1)
+    assert default(8000, 4000) == (T, (12, 2, 4), 1)
+    assert default(3200, 1600) == (T, (16, 1, 4), 2)
+    assert default(1600, 800) == (T, (10, 2, 4), 2)
+    assert default(3200, 1600, bounce=lbm.LBM_BOUNCE_INTERPOLATED, body_r=10.0, body_xc=400, body_yc=800) \
+        == (T, (10, 2, 4), 1)
+    assert default(3200, 1600, kernel=lbm.LBM_KERNEL_TMA_WAVE) == (lbm.LBM_KERNEL_TMA_WAVE, (10, 2, 4), 1)
+    assert default(3200, 1600, storage=lbm.LBM_BF16_SR) == (T, (12, 2, 4), 2)
+    assert default(3200, 1600, storage=lbm.LBM_F64)[0] == lbm.LBM_KERNEL_DIRECT
+    assert default(3200, 1600, consumer_warps=13, cells_per_thread=2, stages=3) == (T, (13, 2, 3), 1)
+    assert default(3200, 1600, ctas_per_sm=1) == (T, (16, 1, 4), 1)
+    with pytest.raises(lbm.LBMError):
+        default(3200, 1600, kernel=lbm.LBM_KERNEL_TMA_WAVE, consumer_warps=16, cells_per_thread=1, stages=6)
     # the multi-step kernel is built for four of the TMA kernel's shapes
     wave = lbm.lbm_kernel_shapes(lbm.LBM_KERNEL_TMA_WAVE)
     assert wave == [(8, 2, 4), (12, 2, 4), (10, 2, 4), (13, 2, 3)]
